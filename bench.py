@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""HMult + relinearisation + rescale throughput of the non-RNS CKKS hot path on GB300.
+
+Workload (one step): a CipherTensor of `cnum` ciphertext pairs at N = 2^16,
+Q = 2^1200, P = 2^1200, scale 2^40 -> fhe_mult_relin_rescale (k = 40).
+Inputs are fresh public-key encryptions of seeded synthetic plaintexts
+(coefficients of an encoded message at scale 2^40), already resident in HBM.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on the
+same workload instead (the reference arm; bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LOGN, LOGQ, LOGP, K_RESCALE = 16, 1200, 1200, 40
+METRIC = "HMult+relin+rescale ciphertexts/s at N=2^16 logQ=1200 (1 GB300)"
+WORKLOAD = "CKKS N=2^16 logQ=logP=1200 scale 2^40: HMult+relin+rescale of a CipherTensor of ciphertext pairs"
+SM_COUNT, SM_MAX_MHZ, IMAD_SLOTS_PER_CLK = 152, 2070.0, 64  # GB300: SMs, max SM clock, IMAD-pipe lanes/SM/clk
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cnum", type=int, default=64, help="ciphertext pairs per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--latency-iters", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- oracle side
+def _oracle_worker_init(seed):
+    global _ORACLE_STATE
+    import fhe_synth as fs
+    from oracle import bigint, ckks
+
+    g = fs.rng(seed)
+    N = 1 << LOGN
+    prm = ckks.CkksParams(LOGN, LOGQ, LOGP)
+    s = [int(x) for x in fs.ternary(g, (), N)]
+    a = bigint.from_limbs(fs.uniform_limbs(g, (), N, LOGQ + LOGP))
+    e = [int(x) for x in fs.gaussian(g, (), N)]
+    evk = ckks.relin_key(prm, s, a, e)
+    la = fs.uniform_limbs(g, (2,), N, LOGQ)
+    lb = fs.uniform_limbs(g, (2,), N, LOGQ)
+    ca = tuple(bigint.from_limbs(la[i]) for i in range(2))
+    cb = tuple(bigint.from_limbs(lb[i]) for i in range(2))
+    _ORACLE_STATE = (evk, ca, cb)
+
+
+def _oracle_step(_):
+    from oracle import ckks
+
+    evk, ca, cb = _ORACLE_STATE
+    t0 = time.perf_counter()
+    ckks.rescale(ckks.mult(ca, cb, evk, LOGQ, LOGP), K_RESCALE, LOGQ)
+    return time.perf_counter() - t0
+
+
+def oracle_throughput(steps: int, warmup: int, workers: int):
+    """Run warmup + timed oracle steps (one ciphertext pair each) on `workers` spawned processes."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(1234,)) as pool:
+        if warmup > 0:
+            pool.map(_oracle_step, range(min(warmup, workers)), chunksize=1)
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_step, range(steps), chunksize=1)
+        wall = time.perf_counter() - t0
+    return steps / wall, wall, per
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    workers = max(1, min(args.steps, cores))
+    value, wall, per = oracle_throughput(args.steps, args.warmup, workers)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ct/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (Python big integers)",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "cnum": 1, "logN": LOGN, "logQ": LOGQ, "logP": LOGP,
+                                        "log_scale": K_RESCALE},
+        "cpu_baseline": {"value": value, "unit": "ct/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{args.steps} ciphertext pairs, one per step, steps spread over {workers} "
+                                   f"spawned processes (one pair per process at a time)"},
+        "e2e": {"value": value, "unit": "ct/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "per_step_s": {"p50": statistics.median(per), "max": max(per)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- roofline counting
+def crt_slots(r: int, out_limbs: int) -> int:
+    """IMAD-pipe slots of one Garner reconstruction (one coefficient), algorithmic count.
+
+    digits: r(r-1)/2 Shoup products (mul.hi = 2 slots, two mul.lo = 2 slots -> 4);
+    Horner: per step the running value's limbs (capped at the output width),
+    one 32x32->64 multiply-add (mad.wide = 2 slots) each.
+    """
+    digits = 4 * r * (r - 1) // 2
+    horner = 0
+    for k in range(r - 2, -1, -1):
+        act = min(out_limbs, (31 * (r - k) + 31) // 32)
+        horner += 2 * act
+    return digits + horner
+
+
+def step_work(fhe, cnum: int) -> dict:
+    """Algorithmic IMAD-pipe slots per step, by kernel class."""
+    N = 1 << LOGN
+    L = (LOGQ + 31) // 32
+    rt = fhe.fhe_primes_for_bound(LOGN + 2 * LOGQ + 1)
+    rk = fhe.fhe_primes_for_bound(LOGN + LOGQ + LOGP + LOGQ)
+    lq_relin = (LOGQ + LOGP + 31) // 32
+    bfly = N // 2 * LOGN
+    return {
+        "crt": cnum * N * (3 * crt_slots(rt, L) + 2 * crt_slots(rk, lq_relin)),
+        "ntt_fwd": cnum * (4 * rt + rk) * bfly * 4,
+        "ntt_inv": cnum * (3 * rt + 2 * rk) * (bfly * 4 + N * 4),
+        "lift": cnum * N * (4 * rt * L + rk * L) * 2,
+        "pointwise": cnum * N * (3 * rt + 2 * rk) * 6,
+        "primes": {"tensor": rt, "keyswitch": rk},
+    }
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2607_05920_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import fhe_synth as fs
+    import paper_2607_05920_gb300 as fhe
+
+    cnum = args.cnum
+    N = 1 << LOGN
+    L = fhe.limbs(LOGQ)
+    g = fs.rng(77 + rank)
+    ctx = fhe.Context(LOGN, LOGQ, LOGP)
+    ctx.keygen(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, LOGQ), fs.gaussian(g, (), N),
+               fs.uniform_limbs(g, (), N, LOGQ + LOGP), fs.gaussian(g, (), N))
+
+    def dev(a):
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint32:
+            a = a.view(np.int32)
+        return torch.from_numpy(a.copy()).cuda()
+
+    def encrypt_batch():
+        m = fs.small_signed(g, (cnum,), N, K_RESCALE + 1)  # encoded-message-sized coefficients
+        # two's complement limbs of m mod 2^logQ (argument marshalling of signed int64 plaintexts)
+        pt = np.zeros((cnum, L, N), dtype=np.uint32)
+        mu = m.astype(np.uint64)
+        pt[:, 0, :] = (mu & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+        pt[:, 1, :] = (mu >> np.uint64(32)).astype(np.uint32)
+        neg = m < 0
+        top = LOGQ - 32 * (L - 1)
+        for l in range(2, L):
+            pt[:, l, :] = np.where(neg, np.uint32(0xFFFFFFFF if (l < L - 1 or top == 32) else (1 << top) - 1), 0)
+        if top < 32:
+            pt[:, L - 1, :] &= np.uint32((1 << top) - 1)
+        return ctx.encrypt(dev(pt), dev(fs.ternary(g, (cnum,), N)), dev(fs.gaussian(g, (cnum,), N)),
+                           dev(fs.gaussian(g, (cnum,), N)))
+
+    A, B = encrypt_batch(), encrypt_batch()
+    out = ctx.empty_ct(cnum, LOGQ - K_RESCALE)
+    ctx.workspace(fhe.FHE_OP_MULT, LOGQ, cnum)
+    torch.cuda.synchronize()
+
+    def step():
+        fhe.fhe_mult_relin_rescale(ctx, A, B, K_RESCALE, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    fhe.fhe_profile_reset(ctx, True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = fhe.fhe_profile_read(ctx)
+    fhe.fhe_profile_reset(ctx, False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * cnum * args.steps / (ms / 1e3)
+    launches = sum(n for n, _ in prof.values())
+
+    # end to end: pinned host inputs -> device, compute, result -> host, every step
+    A_h = A.data.cpu().pin_memory()
+    B_h = B.data.cpu().pin_memory()
+    out_h = torch.empty(out.data.shape, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        A.data.copy_(A_h, non_blocking=True)
+        B.data.copy_(B_h, non_blocking=True)
+        step()
+        out_h.copy_(out.data, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        A.data.copy_(A_h, non_blocking=True)
+        B.data.copy_(B_h, non_blocking=True)
+        step()
+        out_h.copy_(out.data, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * cnum * args.e2e_steps / (ms_e2e / 1e3)
+    h2d = A_h.numel() * 4 + B_h.numel() * 4
+    d2h = out_h.numel() * 4
+
+    # latency of a single pair (cnum = 1)
+    lat = []
+    a1 = fhe.Ciphertext(A.data[:1].clone(), LOGQ)
+    b1 = fhe.Ciphertext(B.data[:1].clone(), LOGQ)
+    o1 = ctx.empty_ct(1, LOGQ - K_RESCALE)
+    for i in range(args.latency_iters + 3):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fhe.fhe_mult_relin_rescale(ctx, a1, b1, K_RESCALE, o1)
+        s1.record(stream)
+        s1.synchronize()
+        if i >= 3:
+            lat.append(s0.elapsed_time(s1))
+    lat.sort()
+
+    work = step_work(fhe, cnum)
+    times = {k: v[1] for k, v in prof.items()}
+    dominant = max((k for k in times if k in work), key=lambda k: times[k])
+    total_slots = work[dominant] * args.steps
+    achieved = total_slots / (times[dominant] / 1e3) / 1e12  # Tslot/s
+    peak = SM_COUNT * IMAD_SLOTS_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    nlaunch_dom = prof[dominant][0]
+    traffic = read_traffic(dominant)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "ct/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded encryptions of encoded-size plaintexts)",
+        "config": {"workload": WORKLOAD, "cnum": cnum, "logN": LOGN, "logQ": LOGQ, "logP": LOGP,
+                   "log_scale": K_RESCALE, "primes": work["primes"],
+                   "l2": f"inputs larger than L2: {2 * A.data.numel() * 4 / 1e9:.2f} GB of ciphertexts per step"},
+        "latency": {"cnum": 1, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                    "iters": len(lat)},
+        "e2e": {"value": e2e_value, "unit": "ct/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "Tslot/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": f"{SM_COUNT} SMs x {IMAD_SLOTS_PER_CLK} IMAD-pipe slots/clk x {SM_MAX_MHZ} MHz",
+                     "launches": nlaunch_dom},
+        "kernels": {k: {"launches": n, "ms": t, "share": t / max(1e-9, sum(times.values()))}
+                    for k, (n, t) in prof.items()},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, wall, per = oracle_throughput(1, 0, 1)
+        result["cpu_baseline"] = {"value": v, "unit": "ct/s", "cores": 1, "kind": "oracle",
+                                  "sample": "one ciphertext pair HMult+relin+rescale at the full workload size "
+                                            f"({wall:.1f} s on one host core)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * fhe.h -- C ABI of libfhe_gb300: the non-RNS CKKS hot path on one GB300 (sm_103a).
+ *
+ * Scheme: the original (non-RNS) CKKS of Cheon et al. as adopted by LibFHE
+ * (Sec. 2 "Fully Homomorphic Encryption", Sec. 3 "Why Original CKKS", Sec. 6).
+ * Ciphertext coefficients are single big integers modulo Q = 2^logQ, stored in
+ * the radix-2^32 limb form of Sec. 4 ("The Radix Representation", 32-bit limbs)
+ * and converted to RNS only inside ring products (Sec. 4 "Hybrid Representation
+ * Strategy"; Sec. 5 pipeline: limb -> RNS -> NTT -> pointwise -> INTT -> Garner
+ * -> limb).  The homomorphic operations follow the paper's operation list
+ * (Sec. 6 "Homomorphic Operation API").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Limb layout ("SoA"): a polynomial with N coefficients of L limbs is
+ *   uint32_t[L][N]: limb l of coefficient i at [l*N + i], least significant
+ *   limb first, N contiguous.  L = ceil(logQ / 32).  Bits at or above logQ
+ *   of the top limb are zero on every output (canonical residues in [0, Q)).
+ * Ciphertext batch (the paper's CipherTensor with batch size cnum, Sec. 6
+ *   "Pairwise and Broadcast Modes"): uint32_t[cnum][2][L][N]; polynomial 0 is
+ *   b, polynomial 1 is a, and decryption is b + a*s (mod Q).
+ * Device vs host: every pointer documented "device" must be a device pointer
+ *   on the context's device; "host" pointers are read synchronously.  The
+ *   caller owns all ciphertext, plaintext and workspace buffers; the library
+ *   never frees them.  Keys, tables and the secret live in memory the context
+ *   owns (allocated through the allocator given at creation).
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   enqueue work and return; results are ready when the stream reaches them.
+ *   Operations on one context may run on several streams only if their
+ *   workspaces differ.
+ * Workspace: operations that need scratch take a caller-allocated device
+ *   buffer `ws` of at least fhe_workspace_bytes(...) bytes (256-byte aligned).
+ * Errors: every int-returning call returns FHE_OK (0) or a negative FHE_E*
+ *   code; fhe_last_error() returns a message for the calling thread.
+ *   Arguments are validated before anything is enqueued; a call that fails
+ *   validation has no effect.  Asynchronous CUDA errors surface as FHE_ECUDA
+ *   on a later call or on fhe_sync().
+ * Aliasing: `out` may alias `in` for fhe_rescale, fhe_moddown, fhe_negate,
+ *   fhe_add and fhe_sub; it must not alias an input of any other operation.
+ */
+#ifndef FHE_GB300_H
+#define FHE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHE_OK 0
+#define FHE_EINVAL (-1)    /* bad argument (null pointer, size or range)          */
+#define FHE_ENOMEM (-2)    /* the context's allocator failed                      */
+#define FHE_ELEVEL (-3)    /* operand levels/ring sizes do not match the request   */
+#define FHE_ENOKEY (-4)    /* no key for the requested operation (keygen missing)  */
+#define FHE_ECUDA (-5)     /* a CUDA runtime call failed                           */
+#define FHE_ETIMEOUT (-6)  /* a bounded device-side wait gave up                   */
+#define FHE_EWORKSPACE (-7)/* workspace null, too small or misaligned              */
+
+#define FHE_SCHEME_CKKS 0
+
+/* Operation codes for fhe_workspace_bytes. */
+#define FHE_OP_MULT 1      /* fhe_mult_relin / fhe_mult_relin_rescale  */
+#define FHE_OP_ROTATE 2    /* fhe_rotate                               */
+#define FHE_OP_ENCRYPT 3   /* fhe_encrypt                              */
+#define FHE_OP_DECRYPT 4   /* fhe_decrypt                              */
+#define FHE_OP_KEYGEN 5    /* fhe_keygen, fhe_keygen_rotation (cnum 1) */
+#define FHE_OP_RING_MUL 6  /* fhe_ring_mul with logQ = max operand bits */
+
+typedef struct fhe_ctx fhe_ctx;
+
+/* Device allocator used for everything the context owns (keys, tables).
+ * alloc returns a device pointer aligned to 256 bytes, or NULL.  With both
+ * NULL the context uses cudaMalloc / cudaFree. */
+typedef void* (*fhe_alloc_fn)(size_t bytes, void* user);
+typedef void (*fhe_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+  int32_t scheme; /* FHE_SCHEME_CKKS                                                  */
+  int32_t logN;   /* ring X^N + 1, N = 2^logN, 3 <= logN <= 16 (Sec. 6 parameter n)   */
+  int32_t logQ;   /* top ciphertext modulus Q = 2^logQ, 1 <= logQ <= 3200 (Sec. 6)     */
+  int32_t logP;   /* special modulus P = 2^logP of the switching keys, 1..3200        */
+} fhe_params;
+
+typedef struct {
+  uint32_t* data; /* device, uint32_t[cnum][2][L][N], L = ceil(logQ/32)               */
+  int32_t cnum;   /* batch size (CipherTensor cnum, Sec. 6)                          */
+  int32_t logQ;   /* this ciphertext's modulus 2^logQ (its level), <= the top logQ   */
+} fhe_ct;
+
+/* Create a context for one ring size and modulus chain.  Computes the NTT
+ * primes (30/31-bit, q = 1 mod 2N; Sec. 4) and the precomputed tables of
+ * Sec. 5 "Precomputation" (bit-reversed psi powers and their inverses,
+ * 2^(32 l) mod q_i, Garner constants [q_j^-1]_{q_k}, prod_{i<k} q_i) and
+ * uploads them.  `alloc`/`free_` may both be NULL (cudaMalloc/cudaFree).
+ * Uses the current CUDA device.  Returns FHE_EINVAL for out-of-range
+ * parameters, FHE_ENOMEM / FHE_ECUDA on allocation or copy failure. */
+int fhe_ctx_create(const fhe_params* params, fhe_alloc_fn alloc, fhe_free_fn free_, void* alloc_user,
+                   fhe_ctx** out);
+
+/* Release everything the context owns (synchronises the device first). */
+int fhe_ctx_destroy(fhe_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fhe_last_error(void);
+
+/* Synchronise the device and report any pending asynchronous CUDA error. */
+int fhe_sync(fhe_ctx* ctx);
+
+/* Bytes of a ciphertext batch: cnum * 2 * ceil(logQ/32) * 2^logN * 4. */
+size_t fhe_ct_bytes(int logN, int logQ, int cnum);
+
+/* Workspace bytes an operation needs for `cnum` ciphertexts at level logQ
+ * (for FHE_OP_RING_MUL: logQ = the larger operand's bits).  0 on bad args. */
+size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum);
+
+/* Key generation (Sec. 6 "Cryptographic Key Management": sk, pk, rk).
+ * All random polynomials are supplied by the caller (host pointers), so that
+ * results are reproducible:
+ *   s     int8_t[N]            secret, coefficients in {-1, 0, 1}
+ *   a_pk  uint32_t[Lq][N]      uniform mod Q,   Lq  = ceil(logQ/32)
+ *   e_pk  int32_t[N]           small error
+ *   a_ev  uint32_t[Lpq][N]     uniform mod P*Q, Lpq = ceil((logP+logQ)/32)
+ *   e_ev  int32_t[N]           small error
+ * Computes on the GPU pk = (-a_pk s + e_pk, a_pk) mod Q and
+ * evk = (-a_ev s + e_ev + P s^2, a_ev) mod P*Q, and keeps them resident
+ * (evk in NTT form over the key-switching primes).  Synchronous. */
+int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk, const uint32_t* a_ev,
+               const int32_t* e_ev);
+
+/* Rotation key for left rotation by `step` slots (Sec. 6 rtk; leftrotate):
+ * rtk = (-a s + e + P s(X^g), a) mod P*Q with g = 5^step mod 2N.
+ * a: host uint32_t[Lpq][N], e: host int32_t[N].  Requires fhe_keygen first.
+ * Replaces an existing key for the same g.  Synchronous. */
+int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e);
+
+/* Public-key encryption (encrypt_pairwise_upon, Sec. 6) of cnum plaintexts:
+ *   out = (v pk_b + m + e0, v pk_a + e1) mod 2^out->logQ
+ * pt: device uint32_t[cnum][L][N], each coefficient m mod 2^logQ (a signed
+ * plaintext in two's complement); v: device int8_t[cnum][N] in {-1,0,1};
+ * e0, e1: device int32_t[cnum][N].  out->data, out->cnum, out->logQ set by
+ * the caller (logQ <= top).  FHE_ENOKEY before fhe_keygen. */
+int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1,
+                fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Decryption (decrypt_pairwise_upon, Sec. 6): m = [b + a s]_Q with the centred
+ * reduction of Sec. 5 ("if x > Q/2, x <- x - Q"), written as L-limb two's
+ * complement (sign-extended to 32 L bits).  pt_out: device uint32_t[cnum][L][N]. */
+int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Homomorphic multiplication with relinearisation (mult_pairwise_into, Sec. 6):
+ *   (d0, d1, d2) = (b1 b2, a1 b2 + a2 b1, a1 a2) mod Q    (Karatsuba, Sec. 5)
+ *   out = (d0, d1) + round(P^-1 (d2 evk_b, d2 evk_a) mod P Q)  (mod Q)
+ * a, b: same cnum and logQ; out: same cnum and logQ, must not alias a or b. */
+int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* ws, size_t ws_bytes,
+                   void* stream);
+
+/* fhe_mult_relin followed by the rescale of fhe_rescale by k bits, fused into
+ * the relinearisation epilogue; out->logQ must equal a->logQ - k. */
+int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Rescale (rescaleBy_pairwise_into, Sec. 6): out = round(in / 2^k) mod
+ * 2^(logQ - k), halves rounded up; out->logQ must equal in->logQ - k. */
+int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream);
+
+/* Modulus drop (moddownBy_pairwise_into, Sec. 6): out = in mod 2^out->logQ,
+ * out->logQ <= in->logQ (scale unchanged). */
+int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
+
+/* Left rotation by `step` slots (leftrotate_broadcast_into, Sec. 6):
+ * kappa_g(X) = X^g, g = 5^step mod 2N, then key switching with rtk_step:
+ *   out = (kappa(b), 0) + round(P^-1 kappa(a) rtk mod P Q)  (mod Q).
+ * FHE_ENOKEY without fhe_keygen_rotation(step).  out must not alias in. */
+int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Limb-domain operations (Sec. 5: add, subtract, negate without RNS). */
+int fhe_add(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream);
+int fhe_sub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream);
+int fhe_negate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
+/* Multiply by a signed integer constant c, |c| < 2^31 (multconst with an
+ * integer-encoded scalar). */
+int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void* stream);
+
+/* The big-integer negacyclic multiplier of Sec. 5 on its own:
+ *   out = a * b mod 2^logOut in Z[X]/(X^N + 1),
+ * a: device uint32_t[cnum][La][N], b: device uint32_t[cnum][Lb][N] (unsigned
+ * canonical limbs), out: device uint32_t[cnum][ceil(logOut/32)][N].
+ * logOut <= 32 (La + Lb) + logN + 1 gives the exact product. */
+int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int Lb, int logOut, uint32_t* out,
+                 int cnum, void* ws, size_t ws_bytes, void* stream);
+
+/* Diagnostics (no counterpart in the paper; measurement support).
+ * Kernel classes: */
+#define FHE_K_LIFT 0      /* limb -> RNS lift                        */
+#define FHE_K_NTT_FWD 1   /* forward NTT passes                      */
+#define FHE_K_NTT_INV 2   /* inverse NTT passes                      */
+#define FHE_K_POINTWISE 3 /* transform-domain products               */
+#define FHE_K_CRT 4       /* Garner reconstruction + fused epilogue  */
+#define FHE_K_LIMB 5      /* limb-domain kernels (rescale, ...)      */
+#define FHE_K_COUNT 6
+/* Reset the per-class counters of `ctx`; with enable != 0, also bracket
+ * every subsequent launch with CUDA events on its stream (adds two event
+ * records per launch).  Not thread-safe with concurrent calls on ctx. */
+int fhe_profile_reset(fhe_ctx* ctx, int enable);
+/* Kernels launched in class `kclass` since the last reset, and (when timing
+ * was enabled) the summed event-measured device time in milliseconds.
+ * Synchronises on the recorded events.  FHE_EINVAL for a bad class. */
+int fhe_profile_read(fhe_ctx* ctx, int kclass, int64_t* launches, double* ms);
+
+/* Number of NTT primes the library uses for a ring product whose exact
+ * result is bounded by 2^bound_bits in absolute value (one spare prime for
+ * the sign, Sec. 5 signed handling).  Informational. */
+int fhe_primes_for_bound(int bound_bits);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHE_GB300_H */

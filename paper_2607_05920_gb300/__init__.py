@@ -1,0 +1,404 @@
+"""Python binding of libfhe_gb300 (include/fhe.h): the non-RNS CKKS hot path on a GB300.
+
+Argument marshalling only.  Every homomorphic step runs in the library's CUDA
+kernels; PyTorch provides device memory (the context's allocator callbacks
+and the caller's tensors) and the current CUDA stream.  The module-level
+functions carry the C ABI's names and signatures with tensors in place of raw
+pointers; ``Context`` bundles them for convenience.
+
+Layouts (see include/fhe.h): a ciphertext batch is a CUDA int32 tensor of
+shape (cnum, 2, L, N) holding uint32 limbs (poly 0 = b, poly 1 = a), least
+significant limb first, L = ceil(logQ / 32).  Plaintexts are (cnum, L, N).
+
+Importing the package loads the shared library and raises ImportError if it
+has not been built (``python -c "import __graft_entry__ as g; g.build()"``):
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfhe_gb300.so")
+
+FHE_OK = 0
+FHE_EINVAL = -1
+FHE_ENOMEM = -2
+FHE_ELEVEL = -3
+FHE_ENOKEY = -4
+FHE_ECUDA = -5
+FHE_ETIMEOUT = -6
+FHE_EWORKSPACE = -7
+FHE_SCHEME_CKKS = 0
+FHE_OP_MULT = 1
+FHE_OP_ROTATE = 2
+FHE_OP_ENCRYPT = 3
+FHE_OP_DECRYPT = 4
+FHE_OP_KEYGEN = 5
+FHE_OP_RING_MUL = 6
+
+
+class FheParams(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("logN", ctypes.c_int32), ("logQ", ctypes.c_int32),
+                ("logP", ctypes.c_int32)]
+
+
+class FheCt(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("cnum", ctypes.c_int32), ("logQ", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes); mirrors include/fhe.h one to one
+SIGNATURES = {
+    "fhe_ctx_create": (_I, [ctypes.POINTER(FheParams), ALLOC_FN, FREE_FN, _P, ctypes.POINTER(_P)]),
+    "fhe_ctx_destroy": (_I, [_P]),
+    "fhe_last_error": (ctypes.c_char_p, []),
+    "fhe_sync": (_I, [_P]),
+    "fhe_ct_bytes": (_SZ, [_I, _I, _I]),
+    "fhe_workspace_bytes": (_SZ, [_P, _I, _I, _I]),
+    "fhe_keygen": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fhe_keygen_rotation": (_I, [_P, _I, _P, _P]),
+    "fhe_encrypt": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_decrypt": (_I, [_P, ctypes.POINTER(FheCt), _P, _P, _SZ, _P]),
+    "fhe_mult_relin": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_mult_relin_rescale": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P,
+                                    _SZ, _P]),
+    "fhe_rescale": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P]),
+    "fhe_moddown": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
+    "fhe_rotate": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_add": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
+    "fhe_sub": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
+    "fhe_negate": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
+    "fhe_mult_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int32, ctypes.POINTER(FheCt), _P]),
+    "fhe_ring_mul": (_I, [_P, _P, _I, _P, _I, _I, _P, _I, _P, _SZ, _P]),
+    "fhe_primes_for_bound": (_I, [_I]),
+    "fhe_profile_reset": (_I, [_P, _I]),
+    "fhe_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+}
+
+KERNEL_CLASSES = ("lift", "ntt_fwd", "ntt_inv", "pointwise", "crt", "limb")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class FheError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib.fhe_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != FHE_OK:
+        raise FheError(rc, where)
+
+
+def limbs(bits: int) -> int:
+    return (int(bits) + 31) // 32
+
+
+@dataclass
+class Ciphertext:
+    """A CipherTensor: data (cnum, 2, L, N) int32 CUDA tensor of uint32 limbs at modulus 2^logQ."""
+
+    data: "object"
+    logQ: int
+
+    @property
+    def cnum(self) -> int:
+        return int(self.data.shape[0])
+
+    def c(self) -> FheCt:
+        return FheCt(self.data.data_ptr(), self.cnum, self.logQ)
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _host(arr, dtype) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(arr), dtype=dtype)
+    return a
+
+
+class Context:
+    """One ring size and modulus chain; owns tables and keys (allocated through torch)."""
+
+    def __init__(self, logN: int, logQ: int, logP: int):
+        import torch
+
+        self.logN, self.logQ, self.logP = int(logN), int(logQ), int(logP)
+        self.N = 1 << self.logN
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._torch = torch
+
+        def _alloc(nbytes, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device.index)
+            except Exception:  # out of memory -> NULL, the library reports FHE_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        prm = FheParams(FHE_SCHEME_CKKS, self.logN, self.logQ, self.logP)
+        h = ctypes.c_void_p()
+        _check(lib.fhe_ctx_create(ctypes.byref(prm), self._alloc_cb, self._free_cb, None, ctypes.byref(h)),
+               "fhe_ctx_create")
+        self.handle = h
+        self._ws = {}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib.fhe_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- memory
+    def workspace(self, op: int, logQ: int, cnum: int):
+        """A cached device workspace large enough for `op` at (logQ, cnum)."""
+        nbytes = lib.fhe_workspace_bytes(self.handle, op, int(logQ), int(cnum))
+        if nbytes == 0:
+            raise FheError(FHE_EINVAL, "fhe_workspace_bytes")
+        cur = self._ws.get(op)
+        if cur is None or cur.numel() < nbytes:
+            cur = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device=self.device)
+            self._ws[op] = cur
+        return cur
+
+    def empty_ct(self, cnum: int, logQ: int) -> Ciphertext:
+        t = self._torch.empty((int(cnum), 2, limbs(logQ), self.N), dtype=self._torch.int32, device=self.device)
+        return Ciphertext(t, int(logQ))
+
+    # ------------------------------------------------------------------ keys
+    def keygen(self, s, a_pk, e_pk, a_ev, e_ev) -> None:
+        fhe_keygen(self, s, a_pk, e_pk, a_ev, e_ev)
+
+    def keygen_rotation(self, step: int, a, e) -> None:
+        fhe_keygen_rotation(self, step, a, e)
+
+    # ------------------------------------------------------------ operations
+    def encrypt(self, pt, v, e0, e1, logQ: int | None = None) -> Ciphertext:
+        out = self.empty_ct(pt.shape[0], self.logQ if logQ is None else logQ)
+        fhe_encrypt(self, pt, v, e0, e1, out)
+        return out
+
+    def decrypt(self, ct: Ciphertext):
+        out = self._torch.empty((ct.cnum, limbs(ct.logQ), self.N), dtype=self._torch.int32, device=self.device)
+        fhe_decrypt(self, ct, out)
+        return out
+
+    def mult_relin(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_mult_relin(self, a, b, out)
+        return out
+
+    def mult_relin_rescale(self, a: Ciphertext, b: Ciphertext, k: int) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ - k)
+        fhe_mult_relin_rescale(self, a, b, k, out)
+        return out
+
+    def rescale(self, ct: Ciphertext, k: int) -> Ciphertext:
+        out = self.empty_ct(ct.cnum, ct.logQ - k)
+        fhe_rescale(self, ct, k, out)
+        return out
+
+    def moddown(self, ct: Ciphertext, logQ: int) -> Ciphertext:
+        out = self.empty_ct(ct.cnum, logQ)
+        fhe_moddown(self, ct, out)
+        return out
+
+    def rotate(self, ct: Ciphertext, step: int) -> Ciphertext:
+        out = self.empty_ct(ct.cnum, ct.logQ)
+        fhe_rotate(self, ct, step, out)
+        return out
+
+    def add(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_add(self, a, b, out)
+        return out
+
+    def sub(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_sub(self, a, b, out)
+        return out
+
+    def negate(self, a: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_negate(self, a, out)
+        return out
+
+    def mult_const(self, a: Ciphertext, c: int) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_mult_const(self, a, c, out)
+        return out
+
+    def ring_mul(self, a, b, logOut: int):
+        cnum = a.shape[0]
+        out = self._torch.empty((cnum, limbs(logOut), self.N), dtype=self._torch.int32, device=self.device)
+        fhe_ring_mul(self, a, b, logOut, out)
+        return out
+
+
+# ------------------------------------------------ C-ABI-named thin wrappers
+def fhe_keygen(ctx: Context, s, a_pk, e_pk, a_ev, e_ev) -> None:
+    N = ctx.N
+    s = _host(s, np.int8).reshape(N)
+    a_pk = _host(a_pk, np.uint32).reshape(limbs(ctx.logQ), N)
+    e_pk = _host(e_pk, np.int32).reshape(N)
+    a_ev = _host(a_ev, np.uint32).reshape(limbs(ctx.logQ + ctx.logP), N)
+    e_ev = _host(e_ev, np.int32).reshape(N)
+    _check(lib.fhe_keygen(ctx.handle, s.ctypes.data, a_pk.ctypes.data, e_pk.ctypes.data, a_ev.ctypes.data,
+                          e_ev.ctypes.data), "fhe_keygen")
+
+
+def fhe_keygen_rotation(ctx: Context, step: int, a, e) -> None:
+    N = ctx.N
+    a = _host(a, np.uint32).reshape(limbs(ctx.logQ + ctx.logP), N)
+    e = _host(e, np.int32).reshape(N)
+    _check(lib.fhe_keygen_rotation(ctx.handle, int(step), a.ctypes.data, e.ctypes.data), "fhe_keygen_rotation")
+
+
+def _dev(t, dtype, shape):
+    import torch
+
+    assert t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == tuple(shape), \
+        (t.dtype, tuple(t.shape), shape)
+    return t.data_ptr()
+
+
+def fhe_encrypt(ctx: Context, pt, v, e0, e1, out: Ciphertext) -> None:
+    import torch
+
+    cnum, L, N = out.cnum, limbs(out.logQ), ctx.N
+    ws = ctx.workspace(FHE_OP_ENCRYPT, ctx.logQ, cnum)
+    oc = out.c()
+    _check(lib.fhe_encrypt(ctx.handle, _dev(pt, torch.int32, (cnum, L, N)), _dev(v, torch.int8, (cnum, N)),
+                           _dev(e0, torch.int32, (cnum, N)), _dev(e1, torch.int32, (cnum, N)), ctypes.byref(oc),
+                           ws.data_ptr(), ws.numel(), _stream()), "fhe_encrypt")
+
+
+def fhe_decrypt(ctx: Context, ct: Ciphertext, out) -> None:
+    import torch
+
+    ws = ctx.workspace(FHE_OP_DECRYPT, ct.logQ, ct.cnum)
+    c = ct.c()
+    _check(lib.fhe_decrypt(ctx.handle, ctypes.byref(c), _dev(out, torch.int32, (ct.cnum, limbs(ct.logQ), ctx.N)),
+                           ws.data_ptr(), ws.numel(), _stream()), "fhe_decrypt")
+
+
+def fhe_mult_relin(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:
+    ws = ctx.workspace(FHE_OP_MULT, a.logQ, a.cnum)
+    ca, cb, co = a.c(), b.c(), out.c()
+    _check(lib.fhe_mult_relin(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), ws.data_ptr(),
+                              ws.numel(), _stream()), "fhe_mult_relin")
+
+
+def fhe_mult_relin_rescale(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, out: Ciphertext) -> None:
+    ws = ctx.workspace(FHE_OP_MULT, a.logQ, a.cnum)
+    ca, cb, co = a.c(), b.c(), out.c()
+    _check(lib.fhe_mult_relin_rescale(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k), ctypes.byref(co),
+                                      ws.data_ptr(), ws.numel(), _stream()), "fhe_mult_relin_rescale")
+
+
+def fhe_rescale(ctx: Context, ct: Ciphertext, k: int, out: Ciphertext) -> None:
+    ci, co = ct.c(), out.c()
+    _check(lib.fhe_rescale(ctx.handle, ctypes.byref(ci), int(k), ctypes.byref(co), _stream()), "fhe_rescale")
+
+
+def fhe_moddown(ctx: Context, ct: Ciphertext, out: Ciphertext) -> None:
+    ci, co = ct.c(), out.c()
+    _check(lib.fhe_moddown(ctx.handle, ctypes.byref(ci), ctypes.byref(co), _stream()), "fhe_moddown")
+
+
+def fhe_rotate(ctx: Context, ct: Ciphertext, step: int, out: Ciphertext) -> None:
+    ws = ctx.workspace(FHE_OP_ROTATE, ct.logQ, ct.cnum)
+    ci, co = ct.c(), out.c()
+    _check(lib.fhe_rotate(ctx.handle, ctypes.byref(ci), int(step), ctypes.byref(co), ws.data_ptr(), ws.numel(),
+                          _stream()), "fhe_rotate")
+
+
+def fhe_add(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:
+    ca, cb, co = a.c(), b.c(), out.c()
+    _check(lib.fhe_add(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()), "fhe_add")
+
+
+def fhe_sub(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:
+    ca, cb, co = a.c(), b.c(), out.c()
+    _check(lib.fhe_sub(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()), "fhe_sub")
+
+
+def fhe_negate(ctx: Context, a: Ciphertext, out: Ciphertext) -> None:
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_negate(ctx.handle, ctypes.byref(ca), ctypes.byref(co), _stream()), "fhe_negate")
+
+
+def fhe_mult_const(ctx: Context, a: Ciphertext, c: int, out: Ciphertext) -> None:
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_mult_const(ctx.handle, ctypes.byref(ca), int(c), ctypes.byref(co), _stream()), "fhe_mult_const")
+
+
+def fhe_ring_mul(ctx: Context, a, b, logOut: int, out) -> None:
+    import torch
+
+    cnum, La, N = a.shape
+    Lb = b.shape[1]
+    ws = ctx.workspace(FHE_OP_RING_MUL, 32 * max(La, Lb), cnum)
+    _check(lib.fhe_ring_mul(ctx.handle, _dev(a, torch.int32, (cnum, La, N)), int(La),
+                            _dev(b, torch.int32, (cnum, Lb, N)), int(Lb), int(logOut),
+                            _dev(out, torch.int32, (cnum, limbs(logOut), N)), int(cnum), ws.data_ptr(), ws.numel(),
+                            _stream()), "fhe_ring_mul")
+
+
+def fhe_primes_for_bound(bound_bits: int) -> int:
+    return int(lib.fhe_primes_for_bound(int(bound_bits)))
+
+
+def fhe_profile_reset(ctx: Context, enable: bool) -> None:
+    _check(lib.fhe_profile_reset(ctx.handle, 1 if enable else 0), "fhe_profile_reset")
+
+
+def fhe_profile_read(ctx: Context) -> dict:
+    """{class name: (launches, milliseconds)} since the last reset."""
+    out = {}
+    for k, name in enumerate(KERNEL_CLASSES):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(lib.fhe_profile_read(ctx.handle, k, ctypes.byref(n), ctypes.byref(ms)), "fhe_profile_read")
+        out[name] = (int(n.value), float(ms.value))
+    return out
+
+
+def fhe_sync(ctx: Context) -> None:
+    _check(lib.fhe_sync(ctx.handle), "fhe_sync")

@@ -1,0 +1,729 @@
+// The C ABI of include/fhe.h: argument checks, workspace carving and the
+// kernel sequence of each homomorphic operation.
+//
+// Ring product (Sec. 5 pipeline): limb -> RNS lift -> forward NTT ->
+// pointwise -> INTT -> Garner -> limb, with the prime count sized to the
+// exact product's bound so the CRT result is the exact integer product.
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace fhe;
+
+namespace {
+
+constexpr int kMaxCnum = 1 << 14;
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("kernel launch failed: %s", cudaGetErrorString(e));
+    return FHE_ECUDA;
+  }
+  return FHE_OK;
+}
+
+#define RET_IF(x)           \
+  do {                      \
+    int _rc = (x);          \
+    if (_rc != FHE_OK) return _rc; \
+  } while (0)
+
+// bump allocator over the caller's workspace
+struct Carve {
+  uint8_t* base;
+  size_t size, used = 0;
+  bool ok = true;
+  Carve(void* p, size_t s) : base((uint8_t*)p), size(s) {}
+  uint32_t* take(size_t words) {
+    size_t b = align256(words * 4);
+    if (!base || used + b > size) {
+      ok = false;
+      return nullptr;
+    }
+    uint32_t* p = (uint32_t*)(base + used);
+    used += b;
+    return p;
+  }
+};
+
+// prime counts of the products (exact bounds; Sec. 5 signed handling needs the spare prime)
+int r_tensor(const fhe_ctx* c, int logQ) { return primes_for_bound(c, c->prm.logN + 2 * logQ + 1); }
+int r_keyswitch(const fhe_ctx* c, int logQ) {
+  return primes_for_bound(c, c->prm.logN + logQ + c->prm.logP + c->prm.logQ);
+}
+int r_enc(const fhe_ctx* c) { return primes_for_bound(c, c->prm.logN + c->prm.logQ); }
+int r_dec(const fhe_ctx* c, int logQ) { return primes_for_bound(c, c->prm.logN + logQ); }
+
+size_t words_mult(const fhe_ctx* c, int logQ, int cnum) {
+  const size_t N = c->N;
+  const int rt = r_tensor(c, logQ), rk = r_keyswitch(c, logQ), L = limbs_for_bits(logQ);
+  if (rt < 0 || rk < 0) return 0;
+  return (size_t)cnum * N * (4 * (size_t)rt + 3 * (size_t)L + 2 * (size_t)rk) + 3 * 64;
+}
+size_t words_rotate(const fhe_ctx* c, int logQ, int cnum) {
+  const size_t N = c->N;
+  const int rk = r_keyswitch(c, logQ), L = limbs_for_bits(logQ);
+  if (rk < 0) return 0;
+  return (size_t)cnum * N * (2 * (size_t)L + 2 * (size_t)rk) + 2 * 64;
+}
+size_t words_encrypt(const fhe_ctx* c, int cnum) {
+  const int re = r_enc(c);
+  if (re < 0) return 0;
+  return (size_t)cnum * c->N * 2 * (size_t)re + 64;
+}
+size_t words_decrypt(const fhe_ctx* c, int logQ, int cnum) {
+  const int rd = r_dec(c, logQ);
+  if (rd < 0) return 0;
+  return (size_t)cnum * c->N * (size_t)rd + 64;
+}
+size_t words_ringmul(const fhe_ctx* c, int bits, int cnum) {
+  const int r = primes_for_bound(c, c->prm.logN + 2 * bits);
+  if (r < 0) return 0;
+  return (size_t)cnum * c->N * 2 * (size_t)r + 2 * 64;
+}
+
+bool ct_ok(const fhe_ctx* ctx, const fhe_ct* ct) {
+  return ct && ct->data && ct->cnum >= 1 && ct->cnum <= kMaxCnum && ct->logQ >= 1 && ct->logQ <= ctx->prm.logQ;
+}
+
+// One ring product C = A * B into limbs through `epi`.  A: La limbs or small
+// int32 (As) / int8 (As8); B: the same.  ws: 2 r N words.  nbatch = 1.
+int ring_product(fhe_ctx* ctx, const uint32_t* A, int La, const int32_t* As, const uint32_t* B, int Lb,
+                 const int32_t* Bs, int r, uint32_t* out, const EpiArgs& epi, uint32_t* ws, cudaStream_t st) {
+  const size_t N = ctx->N;
+  uint32_t* RA = ws;
+  uint32_t* RB = ws + (size_t)r * N;
+  if (A)
+    RET_IF(launch_lift(ctx, A, La, 0, 0, RA, 0, 0, 1, 1, r, st));
+  else
+    RET_IF(launch_lift_small(ctx, As, false, 0, RA, 0, 1, r, st));
+  if (B)
+    RET_IF(launch_lift(ctx, B, Lb, 0, 0, RB, 0, 0, 1, 1, r, st));
+  else
+    RET_IF(launch_lift_small(ctx, Bs, false, 0, RB, 0, 1, r, st));
+  RET_IF(launch_ntt(ctx, ws, 2, r, r, r, false, st));
+  RET_IF(launch_pointwise_mul(ctx, RA, RA, 0, RB, 0, r, 1, st));
+  RET_IF(launch_ntt(ctx, RA, 1, r, r, r, true, st));
+  RET_IF(launch_garner(ctx, RA, 0, 0, r, 1, 1, out, 0, 0, epi, st));
+  return check_launch();
+}
+
+// limbs -> resident NTT form over `rows` primes: dst [npoly][rows][N]
+int to_ntt_form(fhe_ctx* ctx, const uint32_t* src, int L, int npoly, int rows, uint32_t* dst, cudaStream_t st) {
+  const size_t N = ctx->N;
+  RET_IF(launch_lift(ctx, src, L, (size_t)L * N, 0, dst, (size_t)rows * N, 0, npoly, 1, rows, st));
+  RET_IF(launch_ntt(ctx, dst, npoly, rows, rows, rows, false, st));
+  return check_launch();
+}
+
+uint32_t galois_of_step(int N, int step) {
+  // 5 has order N/2 modulo 2N
+  const long long ord = N / 2;
+  long long e = step % ord;
+  if (e < 0) e += ord;
+  uint64_t g = 1, b = 5, m = 2ull * N;
+  while (e) {
+    if (e & 1) g = g * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return (uint32_t)g;
+}
+
+// Shared body of relinearisation and rotation key switching (Sec. 6):
+// Y = [nbatch][2][rk][N] whose block 0 holds the lifted c (limb poly to switch),
+// key K = [2][krows][N]; result (add + round(Y / P)) mod 2^logQ into out.
+int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int nbatch, int logQ, int k2,
+                    const uint32_t* add, size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out,
+                    cudaStream_t st) {
+  const size_t N = ctx->N;
+  RET_IF(launch_ntt(ctx, Y, nbatch, rk, 2 * rk, rk, false, st));
+  RET_IF(launch_pointwise_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
+  RET_IF(launch_ntt(ctx, Y, nbatch * 2, rk, rk, rk, true, st));
+  EpiArgs epi;
+  epi.kind = Epi::kRelin;
+  epi.out_bits = logQ;
+  epi.shift = ctx->prm.logP;
+  epi.k2 = k2;
+  epi.out_limbs = limbs_for_bits(logQ - k2);
+  epi.add = add;
+  epi.add_limbs = limbs_for_bits(logQ);
+  epi.add_pstride = add_pstride;
+  epi.add_bstride = add_bstride;
+  epi.add_polys = add_polys;
+  const size_t Lo = epi.out_limbs;
+  RET_IF(launch_garner(ctx, Y, (size_t)rk * N, 2 * (size_t)rk * N, rk, 2, nbatch, out, Lo * N, 2 * Lo * N, epi, st));
+  return check_launch();
+}
+
+int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* out, void* ws, size_t ws_bytes,
+              void* stream) {
+  if (!ctx || !ct_ok(ctx, a) || !ct_ok(ctx, b) || !ct_ok(ctx, out)) {
+    set_error("mult: null or malformed argument");
+    return FHE_EINVAL;
+  }
+  if (a->logQ != b->logQ || a->cnum != b->cnum || out->cnum != a->cnum) {
+    set_error("mult: operands differ in level or batch size");
+    return FHE_ELEVEL;
+  }
+  if (k2 < 0 || out->logQ != a->logQ - k2 || out->logQ < 1) {
+    set_error("mult: output level %d != %d - %d", out->logQ, a->logQ, k2);
+    return FHE_ELEVEL;
+  }
+  if (!ctx->have_keys) {
+    set_error("mult: no relinearisation key (call fhe_keygen)");
+    return FHE_ENOKEY;
+  }
+  if (out->data == a->data || out->data == b->data) {
+    set_error("mult: out aliases an input");
+    return FHE_EINVAL;
+  }
+  const int logQ = a->logQ, cnum = a->cnum, L = limbs_for_bits(logQ);
+  const int rt = r_tensor(ctx, logQ), rk = r_keyswitch(ctx, logQ);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* X = cv.take((size_t)cnum * 4 * rt * N);
+  uint32_t* D = cv.take((size_t)cnum * 3 * L * N);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("mult: workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ctw = 2 * (size_t)L * N;  // words per input ciphertext
+  // tensor product: lift (b1, a1) and (b2, a2), 4 forward NTTs, Karatsuba, 3 INTTs, Garner
+  RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
+  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
+                     4 * (size_t)rt * N, 2, cnum, rt, st));
+  RET_IF(launch_ntt(ctx, X, cnum * 4, rt, rt, rt, false, st));
+  RET_IF(launch_pointwise_tensor(ctx, X, rt, cnum, st));
+  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  EpiArgs e0;
+  e0.kind = Epi::kStore;
+  e0.out_bits = logQ;
+  e0.out_limbs = L;
+  RET_IF(launch_garner(ctx, X, (size_t)rt * N, 4 * (size_t)rt * N, rt, 3, cnum, D, (size_t)L * N,
+                       3 * (size_t)L * N, e0, st));
+  // relinearisation: d2 -> rk primes, times evk, round(/P), + (d0, d1), optional rescale
+  RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
+                     st));
+  return key_switch_tail(ctx, Y, ctx->evk, rk, cnum, logQ, k2, D, (size_t)L * N, 3 * (size_t)L * N, 2, out->data,
+                         st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fhe_last_error(void) { return fhe::last_error(); }
+
+int fhe_primes_for_bound(int bound_bits) { return primes_for_bound_global(bound_bits); }
+
+int fhe_profile_reset(fhe_ctx* ctx, int enable) {
+  if (!ctx) {
+    set_error("profile_reset: null context");
+    return FHE_EINVAL;
+  }
+  ctx->prof.reset(enable != 0);
+  return FHE_OK;
+}
+
+int fhe_profile_read(fhe_ctx* ctx, int kclass, int64_t* launches, double* ms) {
+  if (!ctx || kclass < 0 || kclass >= FHE_K_COUNT) {
+    set_error("profile_read: bad arguments");
+    return FHE_EINVAL;
+  }
+  if (launches) *launches = ctx->prof.launches[kclass];
+  if (ms) {
+    double total = 0.0;
+    for (auto& pr : ctx->prof.ev[kclass]) {
+      FHE_CHECK_CUDA(cudaEventSynchronize(pr.second));
+      float t = 0.f;
+      FHE_CHECK_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+      total += t;
+    }
+    *ms = total;
+  }
+  return FHE_OK;
+}
+
+size_t fhe_ct_bytes(int logN, int logQ, int cnum) {
+  if (logN < 0 || logN > kMaxLogN || logQ < 1 || cnum < 1) return 0;
+  return (size_t)cnum * 2 * limbs_for_bits(logQ) * ((size_t)1 << logN) * 4;
+}
+
+int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, void* user, fhe_ctx** out) {
+  if (!p || !out) {
+    set_error("ctx_create: null argument");
+    return FHE_EINVAL;
+  }
+  *out = nullptr;
+  if (p->scheme != FHE_SCHEME_CKKS || p->logN < 3 || p->logN > kMaxLogN || p->logQ < 1 || p->logP < 1 ||
+      p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr)) {
+    set_error("ctx_create: parameters out of range (logN %d, logQ %d, logP %d)", p->logN, p->logQ, p->logP);
+    return FHE_EINVAL;
+  }
+  const int R = primes_for_bound_global(p->logN + 2 * p->logQ + p->logP);
+  if (R < 0) {
+    set_error("ctx_create: more than %d primes needed", kMaxPrimes);
+    return FHE_EINVAL;
+  }
+  fhe_ctx* ctx = new fhe_ctx();
+  ctx->prm = *p;
+  ctx->N = 1 << p->logN;
+  ctx->alloc = alloc;
+  ctx->free_ = free_;
+  ctx->alloc_user = user;
+  ctx->R = R;
+  cudaGetDevice(&ctx->device);
+  int rc = build_tables(ctx);
+  if (rc != FHE_OK) {
+    free_all(ctx);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return FHE_OK;
+}
+
+int fhe_ctx_destroy(fhe_ctx* ctx) {
+  if (!ctx) return FHE_OK;
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return FHE_OK;
+}
+
+int fhe_sync(fhe_ctx* ctx) {
+  (void)ctx;
+  FHE_CHECK_CUDA(cudaDeviceSynchronize());
+  FHE_CHECK_CUDA(cudaGetLastError());
+  return FHE_OK;
+}
+
+size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
+  if (!ctx || cnum < 1 || cnum > kMaxCnum || logQ < 1) return 0;
+  size_t w = 0;
+  switch (op) {
+    case FHE_OP_MULT:
+      if (logQ > ctx->prm.logQ) return 0;
+      w = words_mult(ctx, logQ, cnum);
+      break;
+    case FHE_OP_ROTATE:
+      if (logQ > ctx->prm.logQ) return 0;
+      w = words_rotate(ctx, logQ, cnum);
+      break;
+    case FHE_OP_ENCRYPT:
+      w = words_encrypt(ctx, cnum);
+      break;
+    case FHE_OP_DECRYPT:
+      if (logQ > ctx->prm.logQ) return 0;
+      w = words_decrypt(ctx, logQ, cnum);
+      break;
+    case FHE_OP_KEYGEN: {
+      const int r = ctx->R;
+      w = 2 * (size_t)r * ctx->N + 64;
+      break;
+    }
+    case FHE_OP_RING_MUL:
+      w = words_ringmul(ctx, logQ, cnum);
+      break;
+    default:
+      return 0;
+  }
+  return w ? w * 4 + 1024 : 0;
+}
+
+int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk, const uint32_t* a_ev,
+               const int32_t* e_ev) {
+  if (!ctx || !s || !a_pk || !e_pk || !a_ev || !e_ev) {
+    set_error("keygen: null argument");
+    return FHE_EINVAL;
+  }
+  const size_t N = ctx->N;
+  const int logQ = ctx->prm.logQ, logP = ctx->prm.logP;
+  const int Lq = limbs_for_bits(logQ), Lpq = limbs_for_bits(logQ + logP);
+  const int re = r_enc(ctx), rd = r_dec(ctx, logQ), R = ctx->R;
+  // host secret -> int32
+  std::vector<int32_t> s32(N);
+  for (size_t i = 0; i < N; ++i) {
+    if (s[i] < -1 || s[i] > 1) {
+      set_error("keygen: secret coefficient %d out of {-1,0,1}", (int)s[i]);
+      return FHE_EINVAL;
+    }
+    s32[i] = s[i];
+  }
+  // resident key memory (allocated once)
+  if (!ctx->d_s) {
+    ctx->d_s = (int32_t*)ctx_alloc(ctx, N * 4);
+    ctx->d_pk = (uint32_t*)ctx_alloc(ctx, 2 * (size_t)Lq * N * 4);
+    ctx->d_pk_ntt = (uint32_t*)ctx_alloc(ctx, 2 * (size_t)re * N * 4);
+    ctx->d_s_ntt = (uint32_t*)ctx_alloc(ctx, (size_t)rd * N * 4);
+    ctx->evk.ntt = (uint32_t*)ctx_alloc(ctx, 2 * (size_t)R * N * 4);
+    if (!ctx->d_s || !ctx->d_pk || !ctx->d_pk_ntt || !ctx->d_s_ntt || !ctx->evk.ntt) {
+      set_error("keygen: key allocation failed");
+      return FHE_ENOMEM;
+    }
+  }
+  ctx->r_enc = re;
+  ctx->r_dec = rd;
+  ctx->evk.rows = R;
+  // scratch: inputs, s^2, a s, ring-product workspace
+  const size_t scratch_words = (size_t)N * (2 + 1 + 1 + Lq + Lpq + 1 + Lpq + 2 * Lpq) + 2 * (size_t)R * N;
+  uint32_t* scratch = (uint32_t*)ctx_alloc(ctx, scratch_words * 4);
+  if (!scratch) {
+    set_error("keygen: scratch allocation failed");
+    return FHE_ENOMEM;
+  }
+  int32_t* d_epk = (int32_t*)scratch;
+  int32_t* d_eev = d_epk + N;
+  uint32_t* d_apk = (uint32_t*)(d_eev + N);
+  uint32_t* d_aev = d_apk + (size_t)Lq * N;
+  uint32_t* d_s2 = d_aev + (size_t)Lpq * N;        // 1 limb two's complement
+  uint32_t* d_t = d_s2 + N;                        // Lpq limbs two's complement of a_ev s
+  uint32_t* d_evl = d_t + (size_t)Lpq * N;         // [2][Lpq][N] evk limbs
+  uint32_t* rws = d_evl + 2 * (size_t)Lpq * N;     // 2 R N
+  cudaStream_t st = 0;
+  int rc = FHE_OK;
+  auto fail = [&](int code) {
+    ctx_free(ctx, scratch);
+    return code;
+  };
+  if (cudaMemcpy(ctx->d_s, s32.data(), N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_epk, e_pk, N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_eev, e_ev, N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_apk, a_pk, (size_t)Lq * N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_aev, a_ev, (size_t)Lpq * N * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("keygen: upload failed");
+    return fail(FHE_ECUDA);
+  }
+  // pk = (-a s + e, a) mod Q
+  {
+    EpiArgs e;
+    e.kind = Epi::kAddSmall;
+    e.negate = 1;
+    e.small = d_epk;
+    e.out_bits = logQ;
+    e.out_limbs = Lq;
+    rc = ring_product(ctx, d_apk, Lq, nullptr, nullptr, 0, ctx->d_s, re, ctx->d_pk, e, rws, st);
+    if (rc) return fail(rc);
+    if (cudaMemcpy(ctx->d_pk + (size_t)Lq * N, d_apk, (size_t)Lq * N * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+      return fail(FHE_ECUDA);
+  }
+  // s^2 (|.| <= N, one limb two's complement) and a_ev s mod 2^(32 Lpq)
+  {
+    EpiArgs e;
+    e.kind = Epi::kStore;
+    e.out_bits = 32;
+    e.out_limbs = 1;
+    rc = ring_product(ctx, nullptr, 0, ctx->d_s, nullptr, 0, ctx->d_s, primes_for_bound(ctx, ctx->prm.logN + 1),
+                      d_s2, e, rws, st);
+    if (rc) return fail(rc);
+    EpiArgs e2;
+    e2.kind = Epi::kStore;
+    e2.out_bits = 32 * Lpq;
+    e2.out_limbs = Lpq;
+    rc = ring_product(ctx, d_aev, Lpq, nullptr, nullptr, 0, ctx->d_s,
+                      primes_for_bound(ctx, ctx->prm.logN + logQ + logP), d_t, e2, rws, st);
+    if (rc) return fail(rc);
+  }
+  // evk_b = -a s + e + P s^2 mod PQ ; evk_a = a
+  rc = launch_key_combine(ctx, d_t, Lpq, d_eev, d_s2, 1, logP, d_evl, logQ + logP, st);
+  if (rc) return fail(rc);
+  if (cudaMemcpy(d_evl + (size_t)Lpq * N, d_aev, (size_t)Lpq * N * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return fail(FHE_ECUDA);
+  // resident NTT forms
+  if ((rc = to_ntt_form(ctx, d_evl, Lpq, 2, R, ctx->evk.ntt, st))) return fail(rc);
+  if ((rc = to_ntt_form(ctx, ctx->d_pk, Lq, 2, re, ctx->d_pk_ntt, st))) return fail(rc);
+  if ((rc = launch_lift_small(ctx, ctx->d_s, false, 0, ctx->d_s_ntt, 0, 1, rd, st))) return fail(rc);
+  if ((rc = launch_ntt(ctx, ctx->d_s_ntt, 1, rd, rd, rd, false, st))) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    set_error("keygen: device error %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(FHE_ECUDA);
+  }
+  ctx_free(ctx, scratch);
+  ctx->have_keys = true;
+  return FHE_OK;
+}
+
+int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e) {
+  if (!ctx || !a || !e) {
+    set_error("keygen_rotation: null argument");
+    return FHE_EINVAL;
+  }
+  if (!ctx->have_keys) {
+    set_error("keygen_rotation: call fhe_keygen first");
+    return FHE_ENOKEY;
+  }
+  const size_t N = ctx->N;
+  const int logQ = ctx->prm.logQ, logP = ctx->prm.logP;
+  const int Lpq = limbs_for_bits(logQ + logP), R = ctx->R;
+  const uint32_t g = galois_of_step(ctx->N, step);
+  SwitchKey& K = ctx->rtk[g];
+  if (!K.ntt) {
+    K.ntt = (uint32_t*)ctx_alloc(ctx, 2 * (size_t)R * N * 4);
+    K.rows = R;
+    if (!K.ntt) {
+      ctx->rtk.erase(g);
+      set_error("keygen_rotation: allocation failed");
+      return FHE_ENOMEM;
+    }
+  }
+  const size_t scratch_words = (size_t)N * (1 + 1 + Lpq + Lpq + 2 * Lpq) + 2 * (size_t)R * N;
+  uint32_t* scratch = (uint32_t*)ctx_alloc(ctx, scratch_words * 4);
+  if (!scratch) {
+    set_error("keygen_rotation: scratch allocation failed");
+    return FHE_ENOMEM;
+  }
+  auto fail = [&](int code) {
+    ctx_free(ctx, scratch);
+    return code;
+  };
+  int32_t* d_e = (int32_t*)scratch;
+  int32_t* d_ks = d_e + N;  // kappa(s), one limb two's complement
+  uint32_t* d_a = (uint32_t*)(d_ks + N);
+  uint32_t* d_t = d_a + (size_t)Lpq * N;
+  uint32_t* d_kl = d_t + (size_t)Lpq * N;
+  uint32_t* rws = d_kl + 2 * (size_t)Lpq * N;
+  cudaStream_t st = 0;
+  if (cudaMemcpy(d_e, e, N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_a, a, (size_t)Lpq * N * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("keygen_rotation: upload failed");
+    return fail(FHE_ECUDA);
+  }
+  int rc = launch_automorph_small(ctx, ctx->d_s, d_ks, g, st);
+  if (rc) return fail(rc);
+  EpiArgs e2;
+  e2.kind = Epi::kStore;
+  e2.out_bits = 32 * Lpq;
+  e2.out_limbs = Lpq;
+  rc = ring_product(ctx, d_a, Lpq, nullptr, nullptr, 0, ctx->d_s, primes_for_bound(ctx, ctx->prm.logN + logQ + logP),
+                    d_t, e2, rws, st);
+  if (rc) return fail(rc);
+  if ((rc = launch_key_combine(ctx, d_t, Lpq, d_e, (const uint32_t*)d_ks, 1, logP, d_kl, logQ + logP, st)))
+    return fail(rc);
+  if (cudaMemcpy(d_kl + (size_t)Lpq * N, d_a, (size_t)Lpq * N * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return fail(FHE_ECUDA);
+  if ((rc = to_ntt_form(ctx, d_kl, Lpq, 2, R, K.ntt, st))) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    set_error("keygen_rotation: device error");
+    return fail(FHE_ECUDA);
+  }
+  ctx_free(ctx, scratch);
+  return FHE_OK;
+}
+
+int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1, fhe_ct* out,
+                void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !pt || !v || !e0 || !e1 || !ct_ok(ctx, out)) {
+    set_error("encrypt: null or malformed argument");
+    return FHE_EINVAL;
+  }
+  if (!ctx->have_keys) {
+    set_error("encrypt: no public key");
+    return FHE_ENOKEY;
+  }
+  const int cnum = out->cnum, re = ctx->r_enc, logQ = out->logQ, L = limbs_for_bits(logQ);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * re * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("encrypt: workspace too small or misaligned");
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RET_IF(launch_lift_small(ctx, v, true, N, Y, 2 * (size_t)re * N, cnum, re, st));
+  RET_IF(launch_ntt(ctx, Y, cnum, re, 2 * re, re, false, st));
+  SwitchKey pk{ctx->d_pk_ntt, re};
+  RET_IF(launch_pointwise_key(ctx, Y, pk.ntt, pk.rows, re, cnum, st));
+  RET_IF(launch_ntt(ctx, Y, cnum * 2, re, re, re, true, st));
+  EpiArgs e;
+  e.kind = Epi::kAddSmall;
+  e.out_bits = logQ;
+  e.out_limbs = L;
+  e.add = pt;
+  e.add_limbs = L;
+  e.add_bstride = (size_t)L * N;
+  e.add_polys = 1;
+  e.small = e0;
+  e.small1 = e1;
+  e.small_bstride = N;
+  RET_IF(launch_garner(ctx, Y, (size_t)re * N, 2 * (size_t)re * N, re, 2, cnum, out->data, (size_t)L * N,
+                       2 * (size_t)L * N, e, st));
+  return check_launch();
+}
+
+int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !ct_ok(ctx, in) || !pt_out) {
+    set_error("decrypt: null or malformed argument");
+    return FHE_EINVAL;
+  }
+  if (!ctx->have_keys) {
+    set_error("decrypt: no secret key");
+    return FHE_ENOKEY;
+  }
+  const int cnum = in->cnum, logQ = in->logQ, L = limbs_for_bits(logQ), rd = r_dec(ctx, logQ);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* Y = cv.take((size_t)cnum * rd * N);
+  if (!cv.ok || ((uintptr_t)ws & 255) || rd > ctx->r_dec) {
+    set_error("decrypt: workspace too small or misaligned");
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RET_IF(launch_lift(ctx, in->data + (size_t)L * N, L, 0, 2 * (size_t)L * N, Y, 0, (size_t)rd * N, 1, cnum, rd, st));
+  RET_IF(launch_ntt(ctx, Y, cnum, rd, rd, rd, false, st));
+  RET_IF(launch_pointwise_mul(ctx, Y, Y, (size_t)rd * N, ctx->d_s_ntt, 0, rd, cnum, st));
+  RET_IF(launch_ntt(ctx, Y, cnum, rd, rd, rd, true, st));
+  EpiArgs e;
+  e.kind = Epi::kDecrypt;
+  e.out_bits = logQ;
+  e.out_limbs = L;
+  e.add = in->data;
+  e.add_limbs = L;
+  e.add_bstride = 2 * (size_t)L * N;
+  RET_IF(launch_garner(ctx, Y, 0, (size_t)rd * N, rd, 1, cnum, pt_out, 0, (size_t)L * N, e, st));
+  return check_launch();
+}
+
+int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* ws, size_t ws_bytes,
+                   void* stream) {
+  return mult_impl(ctx, a, b, 0, out, ws, ws_bytes, stream);
+}
+
+int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (k < 1) {
+    set_error("mult_relin_rescale: k = %d < 1", k);
+    return FHE_EINVAL;
+  }
+  return mult_impl(ctx, a, b, k, out, ws, ws_bytes, stream);
+}
+
+int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream) {
+  if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || k < 1 || out->logQ != in->logQ - k || out->cnum != in->cnum) {
+    set_error("rescale: bad arguments");
+    return FHE_EINVAL;
+  }
+  if (out->data == in->data && limbs_for_bits(out->logQ) != limbs_for_bits(in->logQ)) {
+    set_error("rescale: in-place rescale must keep the limb count");
+    return FHE_EINVAL;
+  }
+  RET_IF(launch_rescale(ctx, in->data, in->logQ, out->data, k, in->cnum * 2, (cudaStream_t)stream));
+  return check_launch();
+}
+
+int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
+  if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ > in->logQ || out->cnum != in->cnum) {
+    set_error("moddown: bad arguments");
+    return FHE_EINVAL;
+  }
+  if (out->data == in->data && limbs_for_bits(out->logQ) != limbs_for_bits(in->logQ)) {
+    set_error("moddown: in-place drop must keep the limb count");
+    return FHE_EINVAL;
+  }
+  RET_IF(launch_moddown(ctx, in->data, in->logQ, out->data, out->logQ, in->cnum * 2, (cudaStream_t)stream));
+  return check_launch();
+}
+
+static int addsub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, int mode, void* stream) {
+  if (!ctx || !ct_ok(ctx, a) || !ct_ok(ctx, out) || (mode != 2 && !ct_ok(ctx, b))) {
+    set_error("add/sub/negate: bad arguments");
+    return FHE_EINVAL;
+  }
+  if ((mode != 2 && (b->logQ != a->logQ || b->cnum != a->cnum)) || out->logQ != a->logQ || out->cnum != a->cnum) {
+    set_error("add/sub/negate: operand levels differ");
+    return FHE_ELEVEL;
+  }
+  RET_IF(launch_addsub(ctx, a->data, mode == 2 ? a->data : b->data, out->data, a->logQ, a->cnum * 2, mode,
+                       (cudaStream_t)stream));
+  return check_launch();
+}
+int fhe_add(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream) {
+  return addsub(ctx, a, b, out, 0, stream);
+}
+int fhe_sub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream) {
+  return addsub(ctx, a, b, out, 1, stream);
+}
+int fhe_negate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
+  return addsub(ctx, in, nullptr, out, 2, stream);
+}
+int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void* stream) {
+  if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
+      c == INT32_MIN) {
+    set_error("mult_const: bad arguments");
+    return FHE_EINVAL;
+  }
+  RET_IF(launch_mult_const(ctx, in->data, c, out->data, in->logQ, in->cnum * 2, (cudaStream_t)stream));
+  return check_launch();
+}
+
+int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
+      out->data == in->data) {
+    set_error("rotate: bad arguments");
+    return FHE_EINVAL;
+  }
+  const uint32_t g = galois_of_step(ctx->N, step);
+  auto it = ctx->rtk.find(g);
+  if (it == ctx->rtk.end()) {
+    set_error("rotate: no rotation key for step %d (g = %u)", step, g);
+    return FHE_ENOKEY;
+  }
+  const int cnum = in->cnum, logQ = in->logQ, L = limbs_for_bits(logQ), rk = r_keyswitch(ctx, logQ);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* KB = cv.take((size_t)cnum * 2 * L * N);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("rotate: workspace too small or misaligned");
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RET_IF(launch_automorph(ctx, in->data, (size_t)L * N, KB, (size_t)L * N, L, logQ, g, cnum * 2, st));
+  RET_IF(launch_lift(ctx, KB + (size_t)L * N, L, 0, 2 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk, st));
+  return key_switch_tail(ctx, Y, it->second, rk, cnum, logQ, 0, KB, 0, 2 * (size_t)L * N, 1, out->data, st);
+}
+
+int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int Lb, int logOut, uint32_t* out,
+                 int cnum, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !a || !b || !out || La < 1 || Lb < 1 || La > kMaxLiftLimbs || Lb > kMaxLiftLimbs || logOut < 1 ||
+      cnum < 1 || cnum > kMaxCnum) {
+    set_error("ring_mul: bad arguments");
+    return FHE_EINVAL;
+  }
+  const int r = primes_for_bound(ctx, ctx->prm.logN + 32 * (La + Lb));
+  if (r < 0) {
+    set_error("ring_mul: operands too wide for this context's primes");
+    return FHE_EINVAL;
+  }
+  if (limbs_for_bits(logOut) > kMaxLimbs) {
+    set_error("ring_mul: output too wide");
+    return FHE_EINVAL;
+  }
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* RA = cv.take((size_t)cnum * r * N);
+  uint32_t* RB = cv.take((size_t)cnum * r * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("ring_mul: workspace too small or misaligned");
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  RET_IF(launch_lift(ctx, a, La, 0, (size_t)La * N, RA, 0, (size_t)r * N, 1, cnum, r, st));
+  RET_IF(launch_lift(ctx, b, Lb, 0, (size_t)Lb * N, RB, 0, (size_t)r * N, 1, cnum, r, st));
+  RET_IF(launch_ntt(ctx, RA, cnum, r, r, r, false, st));
+  RET_IF(launch_ntt(ctx, RB, cnum, r, r, r, false, st));
+  RET_IF(launch_pointwise_mul(ctx, RA, RA, (size_t)r * N, RB, (size_t)r * N, r, cnum, st));
+  RET_IF(launch_ntt(ctx, RA, cnum, r, r, r, true, st));
+  EpiArgs e;
+  e.kind = Epi::kStore;
+  e.out_bits = logOut;
+  e.out_limbs = limbs_for_bits(logOut);
+  RET_IF(launch_garner(ctx, RA, 0, (size_t)r * N, r, 1, cnum, out, 0, (size_t)e.out_limbs * N, e, st));
+  return check_launch();
+}
+
+}  // extern "C"

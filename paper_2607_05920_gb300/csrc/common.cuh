@@ -1,0 +1,241 @@
+// Internal declarations of libfhe_gb300: the context, the modular arithmetic
+// used by every kernel, and the kernel launchers shared between translation
+// units.  Nothing here is part of the public C ABI (include/fhe.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fhe.h"
+
+namespace fhe {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxPrimes = 256;    // NTT primes available to one context
+constexpr int kMaxLimbs = 128;     // widest big integer a ring product emits (4096 bits)
+constexpr int kMaxLiftLimbs = 128; // widest operand a ring product lifts
+constexpr int kMaxLogN = 16;
+
+// Error reporting (thread-local message, see fhe_last_error).
+void set_error(const char* fmt, ...);
+#define FHE_CHECK_CUDA(expr)                                                     \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      ::fhe::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,               \
+                       cudaGetErrorString(_e));                                  \
+      return FHE_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+// ------------------------------------------------------------ the context
+// A switching key (relinearisation or rotation) in NTT form over the first
+// `rows` primes: uint32_t[2][rows][N] (b' rows, then a' rows).
+struct SwitchKey {
+  uint32_t* ntt = nullptr;
+  int rows = 0;
+};
+
+// Per-kernel-class launch counters and optional CUDA-event timing.
+struct Profile {
+  int64_t launches[FHE_K_COUNT] = {};
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[FHE_K_COUNT];
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get_event();
+  void reset(bool enable);
+  ~Profile();
+};
+
+// Brackets the kernel launches of one launcher call (kernels: how many).
+class ProfScope {
+ public:
+  ProfScope(const fhe_ctx* ctx, int kclass, int kernels, cudaStream_t st);
+  ~ProfScope();
+
+ private:
+  Profile* p_;
+  int k_;
+  cudaStream_t st_;
+  cudaEvent_t stop_ = nullptr;
+};
+
+}  // namespace fhe
+
+struct fhe_ctx {
+  fhe_params prm{};
+  int N = 0;
+  int device = 0;
+  fhe_alloc_fn alloc = nullptr;
+  fhe_free_fn free_ = nullptr;
+  void* alloc_user = nullptr;
+
+  // primes (host copy) and how many the tables cover
+  int R = 0;
+  std::vector<uint32_t> q;
+
+  // device tables (Sec. 5 "Precomputation")
+  uint32_t* d_q = nullptr;        // [R]
+  uint32_t* d_qinv = nullptr;     // [R]  q^-1 mod 2^32 (Montgomery)
+  uint32_t* d_psi = nullptr;      // [R][N] psi^brv(k), forward twiddles (bit-reversed order)
+  uint32_t* d_psi_sh = nullptr;   // [R][N] Shoup companions floor(w 2^32 / q)
+  uint32_t* d_ipsi = nullptr;     // [R][N] psi^-brv(k)
+  uint32_t* d_ipsi_sh = nullptr;  // [R][N]
+  uint32_t* d_nscale = nullptr;   // [R]  N^-1 * 2^32 mod q (INTT scale, undoes one Montgomery factor)
+  uint32_t* d_nscale_sh = nullptr;// [R]
+  uint32_t* d_pow2 = nullptr;     // [R][kMaxLiftLimbs] 2^(32 l) mod q
+  uint32_t* d_red = nullptr;      // [R][4] {2^32 mod q, shoup, 2^64 mod q, shoup}
+  uint2* d_garner = nullptr;      // [R][R] at [k*R + j] = {[q_j^-1]_{q_k}, shoup}, j < k
+  uint32_t* d_mprod = nullptr;    // [R+1][kMaxLimbs] prod_{i<k} q_i mod 2^(32 kMaxLimbs)
+
+  // keys (resident)
+  bool have_keys = false;
+  int32_t* d_s = nullptr;          // [N] secret
+  uint32_t* d_pk = nullptr;        // [2][Lq][N] public key limbs
+  uint32_t* d_pk_ntt = nullptr;    // [2][r_enc][N]
+  int r_enc = 0;
+  uint32_t* d_s_ntt = nullptr;     // [r_dec][N]
+  int r_dec = 0;
+  fhe::SwitchKey evk;
+  std::map<uint32_t, fhe::SwitchKey> rtk;  // by Galois element g
+
+  // diagnostics
+  mutable fhe::Profile prof;
+
+  // every allocation the context owns, for destroy
+  std::vector<std::pair<void*, size_t>> owned;
+};
+
+namespace fhe {
+
+// --------------------------------------------------------- host utilities
+int primes_for_bound(const fhe_ctx* ctx, int bound_bits);  // uses ctx->q
+int primes_for_bound_global(int bound_bits);
+const std::vector<uint32_t>& global_primes();
+void* ctx_alloc(fhe_ctx* ctx, size_t bytes);
+void ctx_free(fhe_ctx* ctx, void* p);
+int build_tables(fhe_ctx* ctx);
+void free_all(fhe_ctx* ctx);
+const char* last_error();
+
+inline int limbs_for_bits(int bits) { return (bits + 31) / 32; }
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------ device arithmetic
+// All primes satisfy 2^30 < q < 2^31, so 2q < 2^32.
+
+// a * w mod q with w's Shoup companion wp = floor(w 2^32 / q); any a < 2^32.
+// Result in [0, q).  (Shoup's precomputed-quotient multiplication.)
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t a, uint32_t w, uint32_t wp, uint32_t q) {
+  uint32_t t = __umulhi(a, wp);
+  uint32_t r = a * w - t * q;  // in [0, 2q)
+  return r >= q ? r - q : r;
+}
+// Same, result left in [0, 2q).
+__device__ __forceinline__ uint32_t shoup_mul_lazy(uint32_t a, uint32_t w, uint32_t wp, uint32_t q) {
+  uint32_t t = __umulhi(a, wp);
+  return a * w - t * q;
+}
+
+// Montgomery product a b 2^-32 mod q for a, b < q, with qinv = q^-1 mod 2^32.
+// (Montgomery 1985.)  Result in [0, q).
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t q, uint32_t qinv) {
+  uint32_t lo = a * b;
+  uint32_t hi = __umulhi(a, b);
+  uint32_t m = lo * qinv;               // m q = lo (mod 2^32)
+  uint32_t mh = __umulhi(m, q);         // (a b - m q) / 2^32 = hi - mh, in (-q, q)
+  uint32_t r = hi - mh;
+  return (hi < mh) ? r + q : r;
+}
+
+__device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t q) {
+  uint32_t s = a + b;  // a, b < q < 2^31: no overflow
+  return s >= q ? s - q : s;
+}
+__device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) {
+  return a >= b ? a - b : a + q - b;
+}
+
+// ------------------------------------------------------------ launchers
+// Lift: residues of unsigned L-limb integers modulo primes [0, r).
+//   src: [npoly][L][N] (poly stride src_stride words), dst: [npoly][r][N]
+//   (poly stride dst_stride words); polys of batch c at src + c*src_bstride.
+int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
+                uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r,
+                cudaStream_t st);
+// Lift of small signed int32 (or int8 when is_i8) coefficients.
+int launch_lift_small(const fhe_ctx* ctx, const void* src, bool is_i8, size_t src_bstride, uint32_t* dst,
+                      size_t dst_bstride, int nbatch, int r, cudaStream_t st);
+
+// In-place negacyclic NTT / INTT on `rows` rows of N words; row k uses prime
+// (k % r) -- rows are grouped [..][r][N].  The inverse includes the scale
+// N^-1 2^32 (one Montgomery factor is undone).
+//  rows are taken in `ngroups` groups of `group_rows` consecutive rows, group g
+//  starting at row g * group_stride; within a group, row k uses prime k % r.
+int launch_ntt(const fhe_ctx* ctx, uint32_t* data, int ngroups, int group_rows, int group_stride, int r,
+               bool inverse, cudaStream_t st);
+
+// Pointwise products in the transform domain (Montgomery; Sec. 5 element-wise
+// arithmetic, Karatsuba of Sec. 5 for the tensor).
+//  tensor: X = [nbatch][4][r][N] holding (B1, A1, B2, A2) -> (D0, D1, D2) in rows 0..3r
+int launch_pointwise_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st);
+//  key: Y = [nbatch][2][r][N]; row block 0 holds D (in), outputs D*K_b into block 0 and
+//  D*K_a into block 1 with K = [2][krows][N] (first r rows used).
+int launch_pointwise_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
+                         cudaStream_t st);
+//  general: Z[b][k][n] = A[b][k][n] * B[(b*bstride_b)][k][n]  (bstride_b 0 = broadcast)
+int launch_pointwise_mul(const fhe_ctx* ctx, uint32_t* Z, const uint32_t* A, size_t a_bstride, const uint32_t* B,
+                         size_t b_bstride, int r, int nbatch, cudaStream_t st);
+
+// Garner reconstruction (Sec. 2 Eq. garner_mrc; Sec. 5 RNS-to-limb) of r
+// residue rows into limbs, with a fused epilogue.
+enum class Epi : int {
+  kStore = 0,     // out = X mod 2^out_bits
+  kRelin = 1,     // out = (add + round(X / 2^shift)) mod 2^out_bits, then optional rescale by k2
+  kAddSmall = 2,  // out = (X + add + small) mod 2^out_bits, add/small optional; negate X first if neg
+  kDecrypt = 3,   // out = centred (X + add) mod 2^out_bits, sign-extended to out limbs
+};
+struct EpiArgs {
+  Epi kind = Epi::kStore;
+  int out_bits = 0;          // modulus 2^out_bits of the result
+  int out_limbs = 0;         // limbs written per coefficient
+  const uint32_t* add = nullptr;  // limbs [L_add][N] per poly (batch stride add_bstride)
+  int add_limbs = 0;
+  size_t add_pstride = 0;    // between polys
+  size_t add_bstride = 0;
+  int add_polys = 1 << 30;   // only polys with index < add_polys receive `add`
+  const int32_t* small = nullptr;  // int32 [N] per batch for poly 0 (batch stride small_bstride)
+  const int32_t* small1 = nullptr; // int32 [N] per batch for poly 1
+  size_t small_bstride = 0;
+  int shift = 0;             // kRelin: log P
+  int k2 = 0;                // kRelin: extra rescale bits (0 = none)
+  int negate = 0;            // kAddSmall: use -X
+};
+// in: [nbatch][npoly][r][N] (poly stride in_pstride, batch in_bstride);
+// out: [nbatch][npoly][out_limbs][N] (strides out_pstride, out_bstride).
+int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, size_t in_bstride, int r, int npoly,
+                  int nbatch, uint32_t* out, size_t out_pstride, size_t out_bstride, const EpiArgs& epi,
+                  cudaStream_t st);
+
+// Limb-domain kernels.
+int launch_rescale(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t* out, int k, int npolys,
+                   cudaStream_t st);
+int launch_moddown(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t* out, int logQ_out, int npolys,
+                   cudaStream_t st);
+int launch_addsub(const fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int logQ, int npolys,
+                  int mode /*0 add,1 sub,2 neg(a)*/, cudaStream_t st);
+int launch_mult_const(const fhe_ctx* ctx, const uint32_t* in, int32_t c, uint32_t* out, int logQ, int npolys,
+                      cudaStream_t st);
+// out[l][n] = sign * in[l][i], kappa_g (X^i -> X^(i g)); polys of L limbs mod 2^logQ.
+int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, uint32_t* out, size_t out_pstride,
+                     int L, int logQ, uint32_t g, int npolys, cudaStream_t st);
+int launch_automorph_small(const fhe_ctx* ctx, const int32_t* in, int32_t* out, uint32_t g, cudaStream_t st);
+// keygen combine: out = (-t + e + (s_from << logP)) mod 2^bits, t two's complement limbs.
+int launch_key_combine(const fhe_ctx* ctx, const uint32_t* t, int Lt, const int32_t* e, const uint32_t* sfrom,
+                       int Ls, int logP, uint32_t* out, int bits, cudaStream_t st);
+
+}  // namespace fhe

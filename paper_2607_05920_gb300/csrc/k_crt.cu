@@ -1,0 +1,259 @@
+// RNS -> limb reconstruction with Garner's mixed-radix conversion (Sec. 2
+// Eq. garner_mrc; Sec. 5 "RNS-to-Limb Reconstruction", "Signed Representation
+// Handling") and a fused epilogue (relinearisation rounding, rescale,
+// additions, centring).
+//
+// Per coefficient (one thread each):
+//  1. digits  v_k = | ((x_k - v_0) c_{0,k} - v_1) c_{1,k} - ... ) c_{k-1,k} |_{q_k},
+//     c_{j,k} = [q_j^-1]_{q_k}, in the nested order of Eq. garner_mrc, with
+//     Shoup multiplications by the precomputed constants; digits are kept in
+//     the thread's shared-memory column.
+//  2. X = v_0 + q_0 (v_1 + q_1 (v_2 + ...)) evaluated by Horner from the top
+//     digit, modulo 2^(32 LB) only (LB register limbs).  The value after the
+//     digits k..r-1 is below 2^(31 (r-k)), so only that many limbs are touched.
+//  3. sign: the prime count leaves the top prime spare (prod_{i<r-1} q_i
+//     exceeds the bound), so the top digit is 0 for a non-negative result and
+//     q_{r-1} - 1 for a negative one; negative results get M = prod q_i
+//     subtracted (mod 2^(32 LB)), giving the two's complement of the signed
+//     exact product.
+//  4. epilogue on the thread's limb column (see Epi in common.cuh).
+#include "common.cuh"
+
+namespace fhe {
+
+constexpr int kCrtThreads = 128;
+
+#define COL(l) sv[(size_t)(l) * kCrtThreads + tid]
+
+// out_bits-bit mask for limb l
+__device__ __forceinline__ uint32_t limb_mask(int l, int bits) {
+  const int rem = bits - 32 * l;
+  if (rem >= 32) return 0xFFFFFFFFu;
+  if (rem <= 0) return 0u;
+  return (1u << rem) - 1u;
+}
+
+// column += 2^pos (mod 2^(32 nl))
+__device__ __forceinline__ void col_add_pow2(uint32_t* sv, int tid, int nl, int pos) {
+  int l = pos >> 5;
+  uint32_t add = 1u << (pos & 31);
+  for (; l < nl && add; ++l) {
+    uint32_t v = COL(l) + add;
+    add = (v < add) ? 1u : 0u;
+    COL(l) = v;
+  }
+}
+
+// column[l] <- (column >> sh)[l] for l < nl_out, reading limbs < nl_in (zero above)
+__device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int nl_in, int nl_out, int sh) {
+  const int sl = sh >> 5, sb = sh & 31;
+  for (int l = 0; l < nl_out; ++l) {
+    const int a = l + sl;
+    uint32_t lo = a < nl_in ? COL(a) : 0u;
+    uint32_t hi = (a + 1) < nl_in ? COL(a + 1) : 0u;
+    COL(l) = sb ? __funnelshift_r(lo, hi, sb) : lo;
+  }
+}
+
+template <int LB>
+__global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restrict__ in, size_t in_pstride,
+                                                        size_t in_bstride, int r, int npoly,
+                                                        uint32_t* __restrict__ out, size_t out_pstride,
+                                                        size_t out_bstride, EpiArgs epi, int N,
+                                                        const uint32_t* __restrict__ qtab,
+                                                        const uint2* __restrict__ gtab, int R,
+                                                        const uint32_t* __restrict__ mprod) {
+  extern __shared__ uint32_t sv[];  // [rows][kCrtThreads], one column per thread
+  const int tid = threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + tid;
+  if (n >= N) return;  // columns are private: no block-wide barrier below
+  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
+  const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
+
+  // 1. mixed-radix digits
+  for (int k = 0; k < r; ++k) {
+    uint32_t x = __ldg(src + (size_t)k * N);
+    const uint32_t qk = __ldg(qtab + k), twoq = 2u * qk;
+    const uint2* crow = gtab + (size_t)k * R;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      const uint2 c0 = __ldg(crow + j), c1 = __ldg(crow + j + 1), c2 = __ldg(crow + j + 2), c3 = __ldg(crow + j + 3);
+      uint32_t d;
+      d = x - COL(j);     if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c0.x, c0.y, qk);
+      d = x - COL(j + 1); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c1.x, c1.y, qk);
+      d = x - COL(j + 2); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c2.x, c2.y, qk);
+      d = x - COL(j + 3); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c3.x, c3.y, qk);
+    }
+    for (; j < k; ++j) {
+      const uint2 c = __ldg(crow + j);
+      uint32_t d = x - COL(j);
+      if ((int32_t)d < 0) d += twoq;  // x - v_j + 2 q_k in (0, 2^32)
+      x = shoup_mul(d, c.x, c.y, qk);
+    }
+    COL(k) = x;
+  }
+
+  // 2. Horner from the top digit, mod 2^(32 LB)
+  uint32_t X[LB];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) X[l] = 0;
+  const uint32_t vtop = COL(r - 1);
+  X[0] = vtop;
+  for (int k = r - 2; k >= 0; --k) {
+    const uint32_t qk = __ldg(qtab + k);
+    uint32_t carry = COL(k);
+    const int act = (31 * (r - k) + 31) >> 5;  // limbs of the running value
+#pragma unroll
+    for (int c = 0; c < LB; c += 8) {
+      if (c < act) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint64_t t = (uint64_t)X[c + u] * qk + carry;
+          X[c + u] = (uint32_t)t;
+          carry = (uint32_t)(t >> 32);
+        }
+      }
+    }
+  }
+
+  // 3. sign from the spare top digit
+  if (vtop > (__ldg(qtab + r - 1) >> 1)) {
+    const uint32_t* M = mprod + (size_t)r * kMaxLimbs;
+    uint32_t borrow = 0;
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const uint64_t d = (uint64_t)X[l] - __ldg(M + l) - borrow;
+      X[l] = (uint32_t)d;
+      borrow = (uint32_t)(d >> 63);
+    }
+  }
+
+  // 4. epilogue on the column
+#pragma unroll
+  for (int l = 0; l < LB; ++l) COL(l) = X[l];
+
+  const int ob = epi.out_bits;
+  int nl = LB;  // live limbs in the column
+  if (epi.kind == Epi::kRelin) {
+    if (epi.shift > 0) col_add_pow2(sv, tid, LB, epi.shift - 1);
+    const int nz = (ob + 31) >> 5;
+    col_shift_right(sv, tid, LB, nz, epi.shift);
+    nl = nz;
+  } else if (epi.kind == Epi::kAddSmall && epi.negate) {
+    uint32_t c = 1;
+    for (int l = 0; l < LB; ++l) {  // -X = ~X + 1
+      const uint32_t v = ~COL(l) + c;
+      c = (c && v == 0) ? 1u : 0u;
+      COL(l) = v;
+    }
+  }
+  const int nlo = (ob + 31) >> 5;  // limbs of the mod-2^ob value
+  if (epi.add && poly < epi.add_polys) {
+    const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n;
+    uint32_t c = 0;
+    for (int l = 0; l < nlo; ++l) {
+      const uint32_t a = l < epi.add_limbs ? __ldg(ad + (size_t)l * N) : 0u;
+      const uint32_t x = l < nl ? COL(l) : 0u;
+      const uint64_t s = (uint64_t)x + a + c;
+      COL(l) = (uint32_t)s;
+      c = (uint32_t)(s >> 32);
+    }
+    nl = nlo;
+  }
+  const int32_t* sm = poly == 0 ? epi.small : (poly == 1 ? epi.small1 : nullptr);
+  if (sm) {
+    const int32_t e = __ldg(sm + (size_t)b * epi.small_bstride + n);
+    const uint32_t ext = e < 0 ? 0xFFFFFFFFu : 0u;
+    uint32_t c = 0;
+    for (int l = 0; l < nlo; ++l) {
+      const uint32_t a = l == 0 ? (uint32_t)e : ext;
+      const uint32_t x = l < nl ? COL(l) : 0u;
+      const uint64_t s = (uint64_t)x + a + c;
+      COL(l) = (uint32_t)s;
+      c = (uint32_t)(s >> 32);
+    }
+    nl = nlo;
+  }
+  for (int l = 0; l < nlo; ++l) COL(l) = (l < nl ? COL(l) : 0u) & limb_mask(l, ob);
+  nl = nlo;
+
+  int fb = ob;  // bits of the final modulus
+  if (epi.kind == Epi::kRelin && epi.k2 > 0) {
+    col_add_pow2(sv, tid, nl, epi.k2 - 1);
+    fb = ob - epi.k2;
+    const int nf = (fb + 31) >> 5;
+    col_shift_right(sv, tid, nl, nf, epi.k2);
+    for (int l = 0; l < nf; ++l) COL(l) &= limb_mask(l, fb);
+    nl = nf;
+  }
+  uint32_t ext = 0;
+  if (epi.kind == Epi::kDecrypt) {
+    // centred (Sec. 5): x > Q/2 -> x - Q, i.e. top bit set and any lower bit set
+    const int tb = fb - 1;
+    const bool top = (COL(tb >> 5) >> (tb & 31)) & 1u;
+    bool low = false;
+    for (int l = 0; l <= (tb >> 5) && !low; ++l) {
+      uint32_t v = COL(l);
+      if (l == (tb >> 5)) v &= (1u << (tb & 31)) - 1u;
+      low = v != 0;
+    }
+    if (top && low) ext = 0xFFFFFFFFu;
+  }
+  uint32_t* dst = out + (size_t)b * out_bstride + (size_t)poly * out_pstride + n;
+  for (int l = 0; l < epi.out_limbs; ++l) {
+    uint32_t v = l < nl ? COL(l) : 0u;
+    if (ext) v |= ~limb_mask(l, fb);
+    dst[(size_t)l * N] = v;
+  }
+}
+
+template <int LB>
+static int garner_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
+                         uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, cudaStream_t st) {
+  const int N = ctx->N;
+  const int threads = kCrtThreads;
+  const int rows = r > LB + 2 ? r : LB + 2;
+  const size_t smem = (size_t)rows * threads * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_garner<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((N + threads - 1) / threads, npoly * nbatch);
+  ProfScope ps(ctx, FHE_K_CRT, 1, st);
+  k_garner<LB><<<grid, threads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q, ctx->d_garner,
+                                             ctx->R, ctx->d_mprod);
+  return FHE_OK;
+}
+
+int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, size_t in_bstride, int r, int npoly,
+                  int nbatch, uint32_t* out, size_t out_pstride, size_t out_bstride, const EpiArgs& epi,
+                  cudaStream_t st) {
+  if (r < 2 || r > ctx->R || npoly < 1 || nbatch < 1 || (size_t)npoly * nbatch > 65535u || epi.out_bits < 1) {
+    set_error("garner: bad sizes r=%d", r);
+    return FHE_EINVAL;
+  }
+  // limbs the reconstruction must carry: enough for the epilogue's reads
+  int need_bits = epi.out_bits + (epi.kind == Epi::kRelin ? epi.shift : 0);
+  int need = (need_bits + 31) / 32;
+  if (epi.out_limbs > need) need = epi.out_limbs;
+  if (need > kMaxLimbs) {
+    set_error("garner: %d limbs exceed %d", need, kMaxLimbs);
+    return FHE_EINVAL;
+  }
+#define FHE_GARNER_CASE(B) \
+  if (need <= B) return garner_launch<B>(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, epi, st);
+  FHE_GARNER_CASE(8)
+  FHE_GARNER_CASE(16)
+  FHE_GARNER_CASE(24)
+  FHE_GARNER_CASE(32)
+  FHE_GARNER_CASE(40)
+  FHE_GARNER_CASE(48)
+  FHE_GARNER_CASE(56)
+  FHE_GARNER_CASE(64)
+  FHE_GARNER_CASE(80)
+  FHE_GARNER_CASE(96)
+  FHE_GARNER_CASE(112)
+  FHE_GARNER_CASE(128)
+#undef FHE_GARNER_CASE
+  return FHE_EINVAL;
+}
+
+}  // namespace fhe

@@ -1,0 +1,278 @@
+// Host side of the context: NTT-friendly primes, the precomputed tables of
+// Sec. 5 "Precomputation for GPU-Accelerated Negacyclic NTT", allocation and
+// error reporting.  Host arithmetic only; uploads with cudaMemcpy.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace fhe {
+
+// ------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+// ------------------------------------------------------- host modular math
+static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+static uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m) {
+  uint64_t r = 1 % m;
+  a %= m;
+  while (e) {
+    if (e & 1) r = mulmod64(r, a, m);
+    a = mulmod64(a, a, m);
+    e >>= 1;
+  }
+  return r;
+}
+static bool is_prime32(uint32_t n) {
+  if (n < 2) return false;
+  // deterministic Miller-Rabin for 32-bit n: bases 2, 7, 61
+  const uint32_t bases[3] = {2, 7, 61};
+  for (uint32_t b : bases)
+    if (n % b == 0) return n == b;
+  uint32_t d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++s;
+  }
+  for (uint32_t b : bases) {
+    uint64_t x = powmod64(b, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < s; ++i) {
+      x = mulmod64(x, x, n);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+static uint32_t inv_mod(uint32_t a, uint32_t q) { return (uint32_t)powmod64(a, q - 2, q); }
+static uint32_t shoup_of(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+
+// Primes q = 1 (mod 2^17), 2^30 < q < 2^31, largest first: NTT-friendly for
+// every N <= 2^16 (Sec. 2: q = 1 mod 2N; Sec. 4: 30-31-bit primes).
+const std::vector<uint32_t>& global_primes() {
+  static std::vector<uint32_t> primes;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const uint32_t step = 1u << 17;
+    for (uint32_t c = 0x80000000u - step + 1; c > 0x40000000u && (int)primes.size() < kMaxPrimes; c -= step)
+      if (is_prime32(c)) primes.push_back(c);
+  });
+  return primes;
+}
+
+// Smallest r with prod_{i<r-1} q_i >= 2^bound_bits: the product is exact and
+// the top prime is a spare whose mixed-radix digit carries the sign.
+int primes_for_bound_global(int bound_bits) {
+  const auto& p = global_primes();
+  double acc = 0.0;
+  for (int r = 1; r <= (int)p.size(); ++r) {
+    // acc = sum_{i<r-1} log2 q_i
+    if (acc >= (double)bound_bits + 1e-6) return r;
+    acc += log2((double)p[r - 1]);
+  }
+  return -1;
+}
+int primes_for_bound(const fhe_ctx* ctx, int bound_bits) {
+  int r = primes_for_bound_global(bound_bits);
+  return (r < 0 || r > ctx->R) ? -1 : r;
+}
+
+void* ctx_alloc(fhe_ctx* ctx, size_t bytes) {
+  bytes = align256(bytes);
+  void* p = nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, ctx->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) ctx->owned.emplace_back(p, bytes);
+  return p;
+}
+
+cudaEvent_t Profile::get_event() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+void Profile::reset(bool enable) {
+  for (int k = 0; k < FHE_K_COUNT; ++k) {
+    launches[k] = 0;
+    for (auto& pr : ev[k]) {
+      pool.push_back(pr.first);
+      pool.push_back(pr.second);
+    }
+    ev[k].clear();
+  }
+  timing = enable;
+}
+Profile::~Profile() {
+  reset(false);
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+ProfScope::ProfScope(const fhe_ctx* ctx, int kclass, int kernels, cudaStream_t st) : p_(&ctx->prof), k_(kclass), st_(st) {
+  p_->launches[k_] += kernels;
+  if (p_->timing) {
+    cudaEvent_t start = p_->get_event();
+    stop_ = p_->get_event();
+    if (start && stop_) {
+      cudaEventRecord(start, st_);
+      p_->ev[k_].emplace_back(start, stop_);
+    } else {
+      stop_ = nullptr;
+    }
+  }
+}
+ProfScope::~ProfScope() {
+  if (stop_) cudaEventRecord(stop_, st_);
+}
+
+void ctx_free(fhe_ctx* ctx, void* p) {
+  for (size_t i = 0; i < ctx->owned.size(); ++i) {
+    if (ctx->owned[i].first == p) {
+      if (ctx->free_)
+        ctx->free_(p, ctx->owned[i].second, ctx->alloc_user);
+      else
+        cudaFree(p);
+      ctx->owned.erase(ctx->owned.begin() + i);
+      return;
+    }
+  }
+}
+
+static unsigned bitrev(unsigned x, int bits) {
+  unsigned r = 0;
+  for (int i = 0; i < bits; ++i) {
+    r = (r << 1) | (x & 1);
+    x >>= 1;
+  }
+  return r;
+}
+
+// Upload helper: allocate + copy, returns nullptr on failure (error set).
+template <typename T>
+static T* upload(fhe_ctx* ctx, const std::vector<T>& h) {
+  T* d = (T*)ctx_alloc(ctx, h.size() * sizeof(T));
+  if (!d) {
+    set_error("device allocation of %zu bytes failed", h.size() * sizeof(T));
+    return nullptr;
+  }
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("table upload failed");
+    return nullptr;
+  }
+  return d;
+}
+
+int build_tables(fhe_ctx* ctx) {
+  const int N = ctx->N, logN = ctx->prm.logN, R = ctx->R;
+  const auto& gp = global_primes();
+  ctx->q.assign(gp.begin(), gp.begin() + R);
+  const std::vector<uint32_t>& q = ctx->q;
+
+  std::vector<uint32_t> qinv(R), nscale(R), nscale_sh(R), red(4 * (size_t)R);
+  std::vector<uint32_t> psi((size_t)R * N), psi_sh((size_t)R * N), ipsi((size_t)R * N), ipsi_sh((size_t)R * N);
+  std::vector<uint32_t> pow2((size_t)R * kMaxLiftLimbs);
+  std::vector<uint2> garner((size_t)R * R, make_uint2(0, 0));
+  std::vector<uint32_t> mprod((size_t)(R + 1) * kMaxLimbs, 0);
+
+  for (int i = 0; i < R; ++i) {
+    const uint32_t qi = q[i];
+    uint32_t inv = 1;  // Newton iteration for q^-1 mod 2^32
+    for (int it = 0; it < 5; ++it) inv *= 2u - qi * inv;
+    qinv[i] = inv;
+    // psi: order exactly 2N (psi^N = -1)
+    uint32_t ps = 0;
+    for (uint32_t x = 2;; ++x) {
+      uint32_t c = (uint32_t)powmod64(x, (qi - 1) / (2ull * N), qi);
+      if (powmod64(c, N, qi) == qi - 1) {
+        ps = c;
+        break;
+      }
+    }
+    const uint32_t ips = inv_mod(ps, qi);
+    for (int k = 0; k < N; ++k) {
+      unsigned e = bitrev((unsigned)k, logN);
+      uint32_t w = (uint32_t)powmod64(ps, e, qi);
+      uint32_t iw = (uint32_t)powmod64(ips, e, qi);
+      psi[(size_t)i * N + k] = w;
+      psi_sh[(size_t)i * N + k] = shoup_of(w, qi);
+      ipsi[(size_t)i * N + k] = iw;
+      ipsi_sh[(size_t)i * N + k] = shoup_of(iw, qi);
+    }
+    // N^-1 * 2^32 mod q: the INTT scale also removes the 2^-32 of one Montgomery product
+    uint32_t ninv = inv_mod((uint32_t)(N % qi), qi);
+    nscale[i] = (uint32_t)mulmod64(ninv, ((uint64_t)1 << 32) % qi, qi);
+    nscale_sh[i] = shoup_of(nscale[i], qi);
+    for (int l = 0; l < kMaxLiftLimbs; ++l) pow2[(size_t)i * kMaxLiftLimbs + l] = (uint32_t)powmod64(2, 32ull * l, qi);
+    uint32_t r32 = (uint32_t)(((uint64_t)1 << 32) % qi);
+    uint32_t r64 = (uint32_t)mulmod64(r32, r32, qi);
+    red[4 * i + 0] = r32;
+    red[4 * i + 1] = shoup_of(r32, qi);
+    red[4 * i + 2] = r64;
+    red[4 * i + 3] = shoup_of(r64, qi);
+  }
+  // Garner constants c_{j,k} = [q_j^-1]_{q_k}, j < k (Sec. 2 Eq. garner_mrc; Sec. 5 CRT constants)
+  for (int k = 0; k < R; ++k)
+    for (int j = 0; j < k; ++j) {
+      uint32_t c = inv_mod(q[j] % q[k], q[k]);
+      garner[(size_t)k * R + j] = make_uint2(c, shoup_of(c, q[k]));
+    }
+  // M_k = prod_{i<k} q_i mod 2^(32 kMaxLimbs) (Sec. 5 CRT constants)
+  std::vector<uint32_t> acc(kMaxLimbs, 0);
+  acc[0] = 1;
+  for (int k = 0; k <= R; ++k) {
+    memcpy(&mprod[(size_t)k * kMaxLimbs], acc.data(), kMaxLimbs * sizeof(uint32_t));
+    if (k == R) break;
+    uint64_t carry = 0;
+    for (int l = 0; l < kMaxLimbs; ++l) {
+      uint64_t t = (uint64_t)acc[l] * q[k] + carry;
+      acc[l] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+
+  if (!(ctx->d_q = upload(ctx, q)) || !(ctx->d_qinv = upload(ctx, qinv)) || !(ctx->d_psi = upload(ctx, psi)) ||
+      !(ctx->d_psi_sh = upload(ctx, psi_sh)) || !(ctx->d_ipsi = upload(ctx, ipsi)) ||
+      !(ctx->d_ipsi_sh = upload(ctx, ipsi_sh)) || !(ctx->d_nscale = upload(ctx, nscale)) ||
+      !(ctx->d_nscale_sh = upload(ctx, nscale_sh)) || !(ctx->d_pow2 = upload(ctx, pow2)) ||
+      !(ctx->d_red = upload(ctx, red)) || !(ctx->d_garner = upload(ctx, garner)) ||
+      !(ctx->d_mprod = upload(ctx, mprod)))
+    return FHE_ENOMEM;
+  return FHE_OK;
+}
+
+void free_all(fhe_ctx* ctx) {
+  for (auto& pr : ctx->owned) {
+    if (ctx->free_)
+      ctx->free_(pr.first, pr.second, ctx->alloc_user);
+    else
+      cudaFree(pr.first);
+  }
+  ctx->owned.clear();
+}
+
+}  // namespace fhe

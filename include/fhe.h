@@ -190,6 +190,28 @@ int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void*
 int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int Lb, int logOut, uint32_t* out,
                  int cnum, void* ws, size_t ws_bytes, void* stream);
 
+/* fhe_mult_relin_rescale for callers that cannot allocate device memory.
+ * The paper has no counterpart; this exists for the library's users.
+ * Some callers cannot call cudaMalloc (or any allocator) where they multiply:
+ * code that runs while a stream is being captured into a CUDA graph, hosts
+ * that forbid allocation after start-up, and plug-ins of other runtimes that
+ * must not touch the process's device allocator.  This call takes no
+ * workspace and allocates nothing (no cudaMalloc/cudaFree, no allocator
+ * callback).  Its scratch is one static device array of 32 MiB that every GPU
+ * loading the library holds until the process exits; a call whose scratch
+ * need (fhe_workspace_bytes(ctx, FHE_OP_MULT, a->logQ, a->cnum)) exceeds
+ * 32 MiB is rejected with FHE_EINVAL before anything is enqueued.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with the context's device current; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (every region is written before it is read, so nothing needs
+ * clearing).  Calls whose GPU work overlaps, for example calls on two streams
+ * of one process, use the same array at the same time: they race and give
+ * wrong results, so issue them on one stream (each process has its own
+ * array).  Arguments and results are as for fhe_mult_relin_rescale. */
+int fhe_mult_relin_rescale_noalloc(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out,
+                                   void* stream);
+
 /* Diagnostics (no counterpart in the paper; measurement support).
  * Kernel classes: */
 #define FHE_K_LIFT 0      /* limb -> RNS lift                        */

@@ -82,6 +82,8 @@ SIGNATURES = {
     "fhe_mult_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int32, ctypes.POINTER(FheCt), _P]),
     "fhe_ring_mul": (_I, [_P, _P, _I, _P, _I, _I, _P, _I, _P, _SZ, _P]),
     "fhe_primes_for_bound": (_I, [_I]),
+    "fhe_mult_relin_rescale_noalloc": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I,
+                                            ctypes.POINTER(FheCt), _P]),
     "fhe_profile_reset": (_I, [_P, _I]),
     "fhe_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
 }
@@ -330,6 +332,13 @@ def fhe_mult_relin_rescale(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, o
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_mult_relin_rescale(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k), ctypes.byref(co),
                                       ws.data_ptr(), ws.numel(), _stream()), "fhe_mult_relin_rescale")
+
+
+def fhe_mult_relin_rescale_noalloc(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, out: Ciphertext) -> None:
+    """fhe_mult_relin_rescale without a workspace, for callers that cannot allocate (static 32 MiB scratch)."""
+    ca, cb, co = a.c(), b.c(), out.c()
+    _check(lib.fhe_mult_relin_rescale_noalloc(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k),
+                                              ctypes.byref(co), _stream()), "fhe_mult_relin_rescale_noalloc")
 
 
 def fhe_rescale(ctx: Context, ct: Ciphertext, k: int, out: Ciphertext) -> None:

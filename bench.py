@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-iters", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--crt", default="direct", choices=["direct", "garner"],
+                    help="RNS->limb reconstruction: exact CRT with rounded quotient, or Garner mixed radix")
     return ap.parse_args()
 
 
@@ -151,6 +153,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- roofline counting
+def crt_slots_direct(r: int, out_limbs: int) -> int:
+    """IMAD-pipe slots of one direct-CRT reconstruction (one coefficient), algorithmic count.
+
+    r Shoup products y_i (4 slots each), r x W limb multiply-adds (mad.wide, 2
+    slots), W multiply-adds for kappa M.
+    """
+    return 4 * r + 2 * r * out_limbs + 2 * out_limbs
+
+
 def crt_slots(r: int, out_limbs: int) -> int:
     """IMAD-pipe slots of one Garner reconstruction (one coefficient), algorithmic count.
 
@@ -166,8 +177,9 @@ def crt_slots(r: int, out_limbs: int) -> int:
     return digits + horner
 
 
-def step_work(fhe, cnum: int) -> dict:
+def step_work(fhe, cnum: int, garner: bool) -> dict:
     """Algorithmic IMAD-pipe slots per step, by kernel class."""
+    cs = crt_slots if garner else crt_slots_direct
     N = 1 << LOGN
     L = (LOGQ + 31) // 32
     rt = fhe.fhe_primes_for_bound(LOGN + 2 * LOGQ + 1)
@@ -175,7 +187,7 @@ def step_work(fhe, cnum: int) -> dict:
     lq_relin = (LOGQ + LOGP + 31) // 32
     bfly = N // 2 * LOGN
     return {
-        "crt": cnum * N * (3 * crt_slots(rt, L) + 2 * crt_slots(rk, lq_relin)),
+        "crt": cnum * N * (3 * cs(rt, L) + 2 * cs(rk, lq_relin)),
         "ntt_fwd": cnum * (4 * rt + rk) * bfly * 4,
         "ntt_inv": cnum * (3 * rt + 2 * rk) * (bfly * 4 + N * 4),
         "lift": cnum * N * (4 * rt * L + rk * L) * 2,
@@ -226,7 +238,8 @@ def run_ours(args):
     N = 1 << LOGN
     L = fhe.limbs(LOGQ)
     g = fs.rng(77 + rank)
-    ctx = fhe.Context(LOGN, LOGQ, LOGP)
+    crt = fhe.FHE_CRT_GARNER if args.crt == "garner" else fhe.FHE_CRT_DIRECT
+    ctx = fhe.Context(LOGN, LOGQ, LOGP, crt=crt)
     ctx.keygen(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, LOGQ), fs.gaussian(g, (), N),
                fs.uniform_limbs(g, (), N, LOGQ + LOGP), fs.gaussian(g, (), N))
 
@@ -333,7 +346,7 @@ def run_ours(args):
             lat.append(s0.elapsed_time(s1))
     lat.sort()
 
-    work = step_work(fhe, cnum)
+    work = step_work(fhe, cnum, args.crt == "garner")
     times = {k: v[1] for k, v in prof.items()}
     dominant = max((k for k in times if k in work), key=lambda k: times[k])
     total_slots = work[dominant] * args.steps
@@ -346,7 +359,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "ct/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded encryptions of encoded-size plaintexts)",
-        "config": {"workload": WORKLOAD, "cnum": cnum, "logN": LOGN, "logQ": LOGQ, "logP": LOGP,
+        "config": {"workload": WORKLOAD, "cnum": cnum, "logN": LOGN, "logQ": LOGQ, "logP": LOGP, "crt": args.crt,
                    "log_scale": K_RESCALE, "primes": work["primes"],
                    "l2": f"inputs larger than L2: {2 * A.data.numel() * 4 / 1e9:.2f} GB of ciphertexts per step"},
         "latency": {"cnum": 1, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],

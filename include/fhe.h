@@ -80,7 +80,13 @@ typedef struct {
   int32_t logN;   /* ring X^N + 1, N = 2^logN, 3 <= logN <= 16 (Sec. 6 parameter n)   */
   int32_t logQ;   /* top ciphertext modulus Q = 2^logQ, 1 <= logQ <= 3200 (Sec. 6)     */
   int32_t logP;   /* special modulus P = 2^logP of the switching keys, 1..3200        */
+  int32_t crt;    /* RNS -> limb reconstruction: FHE_CRT_DIRECT (0, default) or
+                     FHE_CRT_GARNER (1, the mixed-radix form of Sec. 2 Eq. garner_mrc);
+                     both give identical results                                    */
 } fhe_params;
+
+#define FHE_CRT_DIRECT 0 /* exact CRT sum with a rounded quotient (Halevi-Polyakov-Shoup) */
+#define FHE_CRT_GARNER 1 /* Garner's mixed-radix conversion, digits in the nested order   */
 
 typedef struct {
   uint32_t* data; /* device, uint32_t[cnum][2][L][N], L = ceil(logQ/32)               */

@@ -34,6 +34,8 @@ FHE_ECUDA = -5
 FHE_ETIMEOUT = -6
 FHE_EWORKSPACE = -7
 FHE_SCHEME_CKKS = 0
+FHE_CRT_DIRECT = 0
+FHE_CRT_GARNER = 1
 FHE_OP_MULT = 1
 FHE_OP_ROTATE = 2
 FHE_OP_ENCRYPT = 3
@@ -44,7 +46,7 @@ FHE_OP_RING_MUL = 6
 
 class FheParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("logN", ctypes.c_int32), ("logQ", ctypes.c_int32),
-                ("logP", ctypes.c_int32)]
+                ("logP", ctypes.c_int32), ("crt", ctypes.c_int32)]
 
 
 class FheCt(ctypes.Structure):
@@ -150,7 +152,7 @@ def _host(arr, dtype) -> np.ndarray:
 class Context:
     """One ring size and modulus chain; owns tables and keys (allocated through torch)."""
 
-    def __init__(self, logN: int, logQ: int, logP: int):
+    def __init__(self, logN: int, logQ: int, logP: int, crt: int = FHE_CRT_DIRECT):
         import torch
 
         self.logN, self.logQ, self.logP = int(logN), int(logQ), int(logP)
@@ -169,7 +171,8 @@ class Context:
 
         self._alloc_cb = ALLOC_FN(_alloc)
         self._free_cb = FREE_FN(_free)
-        prm = FheParams(FHE_SCHEME_CKKS, self.logN, self.logQ, self.logP)
+        prm = FheParams(FHE_SCHEME_CKKS, self.logN, self.logQ, self.logP, int(crt))
+        self.crt = int(crt)
         h = ctypes.c_void_p()
         _check(lib.fhe_ctx_create(ctypes.byref(prm), self._alloc_cb, self._free_cb, None, ctypes.byref(h)),
                "fhe_ctx_create")

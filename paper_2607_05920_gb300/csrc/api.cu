@@ -261,7 +261,8 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   }
   *out = nullptr;
   if (p->scheme != FHE_SCHEME_CKKS || p->logN < 3 || p->logN > kMaxLogN || p->logQ < 1 || p->logP < 1 ||
-      p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr)) {
+      p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr) ||
+      (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER)) {
     set_error("ctx_create: parameters out of range (logN %d, logQ %d, logP %d)", p->logN, p->logQ, p->logP);
     return FHE_EINVAL;
   }
@@ -277,6 +278,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   ctx->free_ = free_;
   ctx->alloc_user = user;
   ctx->R = R;
+  ctx->crt_mode = p->crt;
   cudaGetDevice(&ctx->device);
   int rc = build_tables(ctx);
   if (rc != FHE_OK) {

@@ -91,6 +91,12 @@ struct fhe_ctx {
   uint32_t* d_red = nullptr;      // [R][4] {2^32 mod q, shoup, 2^64 mod q, shoup}
   uint2* d_garner = nullptr;      // [R][R] at [k*R + j] = {[q_j^-1]_{q_k}, shoup}, j < k
   uint32_t* d_mprod = nullptr;    // [R+1][kMaxLimbs] prod_{i<k} q_i mod 2^(32 kMaxLimbs)
+  // direct CRT over the first r primes, for every r in [1, R]; rows of set r start at r(r-1)/2
+  uint32_t* d_crt_qhat = nullptr; // [R(R+1)/2][kMaxLimbs] (M_r / q_i) mod 2^(32 kMaxLimbs)
+  uint2* d_crt_inv = nullptr;     // [R(R+1)/2] {[(M_r / q_i)^-1]_{q_i}, shoup}
+  uint32_t* d_crt_negm = nullptr; // [R+1][kMaxLimbs] (-M_r) mod 2^(32 kMaxLimbs)
+  float* d_invq = nullptr;        // [R] 1/q_i rounded to fp32
+  int crt_mode = 0;               // 0 direct CRT, 1 Garner (Eq. garner_mrc)
 
   // keys (resident)
   bool have_keys = false;

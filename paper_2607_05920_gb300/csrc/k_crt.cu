@@ -55,82 +55,12 @@ __device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int nl_in
   }
 }
 
-template <int LB>
-__global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restrict__ in, size_t in_pstride,
-                                                        size_t in_bstride, int r, int npoly,
-                                                        uint32_t* __restrict__ out, size_t out_pstride,
-                                                        size_t out_bstride, EpiArgs epi, int N,
-                                                        const uint32_t* __restrict__ qtab,
-                                                        const uint2* __restrict__ gtab, int R,
-                                                        const uint32_t* __restrict__ mprod) {
-  extern __shared__ uint32_t sv[];  // [rows][kCrtThreads], one column per thread
-  const int tid = threadIdx.x;
-  const int n = blockIdx.x * blockDim.x + tid;
-  if (n >= N) return;  // columns are private: no block-wide barrier below
-  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
-  const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
-
-  // 1. mixed-radix digits
-  for (int k = 0; k < r; ++k) {
-    uint32_t x = __ldg(src + (size_t)k * N);
-    const uint32_t qk = __ldg(qtab + k), twoq = 2u * qk;
-    const uint2* crow = gtab + (size_t)k * R;
-    int j = 0;
-    for (; j + 4 <= k; j += 4) {
-      const uint2 c0 = __ldg(crow + j), c1 = __ldg(crow + j + 1), c2 = __ldg(crow + j + 2), c3 = __ldg(crow + j + 3);
-      uint32_t d;
-      d = x - COL(j);     if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c0.x, c0.y, qk);
-      d = x - COL(j + 1); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c1.x, c1.y, qk);
-      d = x - COL(j + 2); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c2.x, c2.y, qk);
-      d = x - COL(j + 3); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c3.x, c3.y, qk);
-    }
-    for (; j < k; ++j) {
-      const uint2 c = __ldg(crow + j);
-      uint32_t d = x - COL(j);
-      if ((int32_t)d < 0) d += twoq;  // x - v_j + 2 q_k in (0, 2^32)
-      x = shoup_mul(d, c.x, c.y, qk);
-    }
-    COL(k) = x;
-  }
-
-  // 2. Horner from the top digit, mod 2^(32 LB)
-  uint32_t X[LB];
-#pragma unroll
-  for (int l = 0; l < LB; ++l) X[l] = 0;
-  const uint32_t vtop = COL(r - 1);
-  X[0] = vtop;
-  for (int k = r - 2; k >= 0; --k) {
-    const uint32_t qk = __ldg(qtab + k);
-    uint32_t carry = COL(k);
-    const int act = (31 * (r - k) + 31) >> 5;  // limbs of the running value
-#pragma unroll
-    for (int c = 0; c < LB; c += 8) {
-      if (c < act) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const uint64_t t = (uint64_t)X[c + u] * qk + carry;
-          X[c + u] = (uint32_t)t;
-          carry = (uint32_t)(t >> 32);
-        }
-      }
-    }
-  }
-
-  // 3. sign from the spare top digit
-  if (vtop > (__ldg(qtab + r - 1) >> 1)) {
-    const uint32_t* M = mprod + (size_t)r * kMaxLimbs;
-    uint32_t borrow = 0;
-#pragma unroll
-    for (int l = 0; l < LB; ++l) {
-      const uint64_t d = (uint64_t)X[l] - __ldg(M + l) - borrow;
-      X[l] = (uint32_t)d;
-      borrow = (uint32_t)(d >> 63);
-    }
-  }
-
-  // 4. epilogue on the column
-#pragma unroll
-  for (int l = 0; l < LB; ++l) COL(l) = X[l];
+// Epilogue on the thread's limb column, which holds X mod 2^(32 LB) in rows
+// [0, LB): relinearisation rounding / rescale / additions / centring per
+// EpiArgs, then the store of epi.out_limbs limbs.
+__device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, int LB, const EpiArgs& epi, int poly,
+                                          int b, int n, int N, uint32_t* __restrict__ out, size_t out_pstride,
+                                          size_t out_bstride) {
 
   const int ob = epi.out_bits;
   int nl = LB;  // live limbs in the column
@@ -207,6 +137,175 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
   }
 }
 
+
+template <int LB>
+__global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restrict__ in, size_t in_pstride,
+                                                        size_t in_bstride, int r, int npoly,
+                                                        uint32_t* __restrict__ out, size_t out_pstride,
+                                                        size_t out_bstride, EpiArgs epi, int N,
+                                                        const uint32_t* __restrict__ qtab,
+                                                        const uint2* __restrict__ gtab, int R,
+                                                        const uint32_t* __restrict__ mprod) {
+  extern __shared__ uint32_t sv[];  // [rows][kCrtThreads], one column per thread
+  const int tid = threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + tid;
+  if (n >= N) return;  // columns are private: no block-wide barrier below
+  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
+  const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
+
+  // 1. mixed-radix digits
+  for (int k = 0; k < r; ++k) {
+    uint32_t x = __ldg(src + (size_t)k * N);
+    const uint32_t qk = __ldg(qtab + k), twoq = 2u * qk;
+    const uint2* crow = gtab + (size_t)k * R;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      const uint2 c0 = __ldg(crow + j), c1 = __ldg(crow + j + 1), c2 = __ldg(crow + j + 2), c3 = __ldg(crow + j + 3);
+      uint32_t d;
+      d = x - COL(j);     if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c0.x, c0.y, qk);
+      d = x - COL(j + 1); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c1.x, c1.y, qk);
+      d = x - COL(j + 2); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c2.x, c2.y, qk);
+      d = x - COL(j + 3); if ((int32_t)d < 0) d += twoq; x = shoup_mul(d, c3.x, c3.y, qk);
+    }
+    for (; j < k; ++j) {
+      const uint2 c = __ldg(crow + j);
+      uint32_t d = x - COL(j);
+      if ((int32_t)d < 0) d += twoq;  // x - v_j + 2 q_k in (0, 2^32)
+      x = shoup_mul(d, c.x, c.y, qk);
+    }
+    COL(k) = x;
+  }
+
+  // 2. Horner from the top digit, mod 2^(32 LB)
+  uint32_t X[LB];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) X[l] = 0;
+  const uint32_t vtop = COL(r - 1);
+  X[0] = vtop;
+  for (int k = r - 2; k >= 0; --k) {
+    const uint32_t qk = __ldg(qtab + k);
+    uint32_t carry = COL(k);
+    const int act = (31 * (r - k) + 31) >> 5;  // limbs of the running value
+#pragma unroll
+    for (int c = 0; c < LB; c += 8) {
+      if (c < act) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint64_t t = (uint64_t)X[c + u] * qk + carry;
+          X[c + u] = (uint32_t)t;
+          carry = (uint32_t)(t >> 32);
+        }
+      }
+    }
+  }
+
+  // 3. sign from the spare top digit
+  if (vtop > (__ldg(qtab + r - 1) >> 1)) {
+    const uint32_t* M = mprod + (size_t)r * kMaxLimbs;
+    uint32_t borrow = 0;
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const uint64_t d = (uint64_t)X[l] - __ldg(M + l) - borrow;
+      X[l] = (uint32_t)d;
+      borrow = (uint32_t)(d >> 63);
+    }
+  }
+
+  // 4. epilogue on the column
+#pragma unroll
+  for (int l = 0; l < LB; ++l) COL(l) = X[l];
+  crt_epilogue(sv, tid, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
+}
+
+
+// ------------------------------------------------------------- direct CRT
+// Exact CRT with a rounded quotient (the floating-point quotient of
+// Halevi-Polyakov-Shoup 2019, "An improved RNS variant of the BFV scheme"):
+//   y_i = [x_i (M/q_i)^-1]_{q_i},   X = sum_i y_i (M/q_i) - kappa M,
+//   kappa = round(sum_i y_i / q_i).
+// sum_i y_i / q_i = kappa + X/M exactly, and |X| < prod_{i<r-1} q_i = M/q_{r-1}
+// (the prime count's spare prime) gives |X/M| < 2^-30; the fp32 sum has an
+// absolute error below 2^-8 for r <= 256 terms, so round() returns kappa
+// exactly and X comes out signed (two's complement mod 2^(32 LB)).  The
+// dense part sum_i y_i (M/q_i) is a [coefficients x r] by [r x LB-limbs]
+// product: one 32x32->64 multiply-add per (prime, limb), with the constant
+// rows staged in shared memory and read as 128-bit broadcasts.
+template <int LB>
+__global__ void __launch_bounds__(kCrtThreads) k_crt_direct(const uint32_t* __restrict__ in, size_t in_pstride,
+                                                            size_t in_bstride, int r, int npoly,
+                                                            uint32_t* __restrict__ out, size_t out_pstride,
+                                                            size_t out_bstride, EpiArgs epi, int N,
+                                                            const uint32_t* __restrict__ qtab,
+                                                            const uint2* __restrict__ cinv,
+                                                            const uint32_t* __restrict__ qhat,
+                                                            const uint32_t* __restrict__ negm,
+                                                            const float* __restrict__ invq) {
+  extern __shared__ uint32_t sv[];  // first the [r][LB] constant rows, then the [LB+2][T] limb columns
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < r * LB; idx += blockDim.x) sv[idx] = __ldg(qhat + (size_t)(idx / LB) * kMaxLimbs + idx % LB);
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + tid;
+  const bool active = n < N;
+  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
+  uint32_t acc[LB];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) acc[l] = 0;
+  if (active) {
+    const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
+    float fs = 0.f;
+    for (int i = 0; i < r; ++i) {
+      const uint32_t x = __ldg(src + (size_t)i * N);
+      const uint2 ci = __ldg(cinv + i);
+      const uint32_t y = shoup_mul(x, ci.x, ci.y, __ldg(qtab + i));
+      fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
+      const uint4* Q = reinterpret_cast<const uint4*>(sv + i * LB);
+      uint32_t c = 0;
+#pragma unroll
+      for (int l4 = 0; l4 < LB / 4; ++l4) {
+        const uint4 qv = Q[l4];
+        uint64_t t;
+        t = (uint64_t)y * qv.x + acc[4 * l4 + 0]; t += c; acc[4 * l4 + 0] = (uint32_t)t; c = (uint32_t)(t >> 32);
+        t = (uint64_t)y * qv.y + acc[4 * l4 + 1]; t += c; acc[4 * l4 + 1] = (uint32_t)t; c = (uint32_t)(t >> 32);
+        t = (uint64_t)y * qv.z + acc[4 * l4 + 2]; t += c; acc[4 * l4 + 2] = (uint32_t)t; c = (uint32_t)(t >> 32);
+        t = (uint64_t)y * qv.w + acc[4 * l4 + 3]; t += c; acc[4 * l4 + 3] = (uint32_t)t; c = (uint32_t)(t >> 32);
+      }
+    }
+    // X = acc - kappa M = acc + kappa (-M)  (mod 2^(32 LB))
+    const uint32_t kappa = (uint32_t)__float2int_rn(fs);
+    uint32_t c = 0;
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      uint64_t t = (uint64_t)kappa * __ldg(negm + l) + acc[l];
+      t += c;
+      acc[l] = (uint32_t)t;
+      c = (uint32_t)(t >> 32);
+    }
+  }
+  __syncthreads();  // the constant rows are dead: the area becomes the limb columns
+  if (!active) return;
+#pragma unroll
+  for (int l = 0; l < LB; ++l) COL(l) = acc[l];
+  crt_epilogue(sv, tid, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
+}
+
+template <int LB>
+static int direct_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
+                         uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, cudaStream_t st) {
+  const int N = ctx->N;
+  const int threads = kCrtThreads;
+  const size_t rows_words = (size_t)r * LB, col_words = (size_t)(LB + 2) * threads;
+  const size_t smem = 4 * (rows_words > col_words ? rows_words : col_words);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_crt_direct<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((N + threads - 1) / threads, npoly * nbatch);
+  ProfScope ps(ctx, FHE_K_CRT, 1, st);
+  const size_t off = (size_t)r * (r - 1) / 2;
+  k_crt_direct<LB><<<grid, threads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q,
+                                                 ctx->d_crt_inv + off, ctx->d_crt_qhat + off * kMaxLimbs,
+                                                 ctx->d_crt_negm + (size_t)r * kMaxLimbs, ctx->d_invq);
+  return FHE_OK;
+}
+
 template <int LB>
 static int garner_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
                          uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, cudaStream_t st) {
@@ -238,8 +337,13 @@ int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, siz
     set_error("garner: %d limbs exceed %d", need, kMaxLimbs);
     return FHE_EINVAL;
   }
-#define FHE_GARNER_CASE(B) \
-  if (need <= B) return garner_launch<B>(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, epi, st);
+#define FHE_GARNER_CASE(B)                                                                                       \
+  if (need <= B)                                                                                                 \
+    return ctx->crt_mode == 1                                                                                    \
+               ? garner_launch<B>(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, \
+                                  epi, st)                                                                       \
+               : direct_launch<B>(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, \
+                                  epi, st);
   FHE_GARNER_CASE(8)
   FHE_GARNER_CASE(16)
   FHE_GARNER_CASE(24)

@@ -255,6 +255,56 @@ int build_tables(fhe_ctx* ctx) {
     }
   }
 
+  // Direct CRT constants for every prime-prefix size r (built incrementally:
+  // adding prime q_r multiplies each M_r / q_i by q_r and appends M_r itself).
+  const size_t nrows = (size_t)R * (R + 1) / 2;
+  std::vector<uint32_t> qhat(nrows * kMaxLimbs, 0), negm((size_t)(R + 1) * kMaxLimbs, 0);
+  std::vector<uint2> crt_inv(nrows);
+  std::vector<float> invq(R);
+  {
+    std::vector<uint32_t> cur((size_t)R * kMaxLimbs, 0);  // cur[i] = prod_{j<r, j!=i} q_j mod 2^4096
+    std::vector<uint32_t> Mr(kMaxLimbs, 0);               // M_r mod 2^4096
+    std::vector<uint64_t> pm(R, 1);                       // prod_{j<r, j!=i} q_j mod q_i
+    Mr[0] = 1;
+    auto mul_word = [](uint32_t* x, uint32_t w) {
+      uint64_t c = 0;
+      for (int l = 0; l < kMaxLimbs; ++l) {
+        uint64_t t = (uint64_t)x[l] * w + c;
+        x[l] = (uint32_t)t;
+        c = t >> 32;
+      }
+    };
+    for (int r = 1; r <= R; ++r) {
+      // extend from r-1 primes to r primes: new prime q_{r-1}
+      const uint32_t qn = q[r - 1];
+      for (int i = 0; i < r - 1; ++i) {
+        mul_word(&cur[(size_t)i * kMaxLimbs], qn);
+        pm[i] = pm[i] * (qn % q[i]) % q[i];
+      }
+      memcpy(&cur[(size_t)(r - 1) * kMaxLimbs], Mr.data(), kMaxLimbs * 4);  // M_{r-1} = prod_{j<r-1} q_j
+      uint64_t pr = 1;
+      for (int j = 0; j < r - 1; ++j) pr = pr * (q[j] % qn) % qn;
+      pm[r - 1] = pr;
+      mul_word(Mr.data(), qn);  // M_r
+      const size_t off = (size_t)r * (r - 1) / 2;
+      for (int i = 0; i < r; ++i) {
+        memcpy(&qhat[(off + i) * kMaxLimbs], &cur[(size_t)i * kMaxLimbs], kMaxLimbs * 4);
+        const uint32_t inv = inv_mod((uint32_t)pm[i], q[i]);
+        crt_inv[off + i] = make_uint2(inv, shoup_of(inv, q[i]));
+      }
+      uint64_t c = 1;  // -M_r = ~M_r + 1
+      for (int l = 0; l < kMaxLimbs; ++l) {
+        uint64_t t = (uint64_t)(uint32_t)~Mr[l] + c;
+        negm[(size_t)r * kMaxLimbs + l] = (uint32_t)t;
+        c = t >> 32;
+      }
+    }
+    for (int i = 0; i < R; ++i) invq[i] = (float)(1.0 / (double)q[i]);
+  }
+
+  if (!(ctx->d_crt_qhat = upload(ctx, qhat)) || !(ctx->d_crt_inv = upload(ctx, crt_inv)) ||
+      !(ctx->d_crt_negm = upload(ctx, negm)) || !(ctx->d_invq = upload(ctx, invq)))
+    return FHE_ENOMEM;
   if (!(ctx->d_q = upload(ctx, q)) || !(ctx->d_qinv = upload(ctx, qinv)) || !(ctx->d_psi = upload(ctx, psi)) ||
       !(ctx->d_psi_sh = upload(ctx, psi_sh)) || !(ctx->d_ipsi = upload(ctx, ipsi)) ||
       !(ctx->d_ipsi_sh = upload(ctx, ipsi_sh)) || !(ctx->d_nscale = upload(ctx, nscale)) ||

@@ -25,7 +25,7 @@ class Pair:
     rtk: dict
 
 
-def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=()):
+def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=(), crt=0):
     import paper_2607_05920_gb300 as fhe
 
     g = fs.rng(seed)
@@ -35,7 +35,7 @@ def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=()):
     e_pk = fs.gaussian(g, (), N)
     a_ev = fs.uniform_limbs(g, (), N, logQ + logP)
     e_ev = fs.gaussian(g, (), N)
-    ctx = fhe.Context(logN, logQ, logP)
+    ctx = fhe.Context(logN, logQ, logP, crt=crt)
     ctx.keygen(s, a_pk, e_pk, a_ev, e_ev)
     prm = ckks.CkksParams(logN, logQ, logP)
     si = [int(x) for x in s]

@@ -27,12 +27,13 @@ def _oracle_ct(limbs):
     return [tuple(bigint.from_limbs(limbs[c, p]) for p in range(2)) for c in range(limbs.shape[0])]
 
 
+@pytest.mark.parametrize("crt", [0, 1], ids=["direct_crt", "garner"])
 @pytest.mark.parametrize("logN,La,Lb,logOut", [(11, 4, 4, 268), (11, 3, 1, 100), (8, 1, 1, 64), (14, 5, 7, 200),
-                                                (16, 2, 3, 64)])
-def test_ring_mul_matches_exact_product(logN, La, Lb, logOut):
+                                                (16, 2, 3, 64), (12, 40, 40, 2600)])
+def test_ring_mul_matches_exact_product(logN, La, Lb, logOut, crt):
     import paper_2607_05920_gb300 as fhe
 
-    ctx = fhe.Context(logN, 200, 200)
+    ctx = fhe.Context(logN, 1300, 1300, crt=crt)
     g = fs.rng(logN * 100 + La)
     N = 1 << logN
     cnum = 2
@@ -50,10 +51,10 @@ def test_ring_mul_matches_exact_product(logN, La, Lb, logOut):
     ctx.close()
 
 
-@pytest.fixture(scope="module")
-def c1():
-    # N = 2^11, Q = P = 2^120 (the smallest workload), plus rotation keys
-    return make_pair(11, 120, 120, seed=11, rot_steps=(1, 3, -1, 1 << 10))
+@pytest.fixture(scope="module", params=[0, 1], ids=["direct_crt", "garner"])
+def c1(request):
+    # N = 2^11, Q = P = 2^120 (the smallest workload), plus rotation keys; both reconstructions
+    return make_pair(11, 120, 120, seed=11, rot_steps=(1, 3, -1, 1 << 10), crt=request.param)
 
 
 def _messages(P, count, log_scale=30):
@@ -140,9 +141,10 @@ def test_decoded_product_accuracy_c1(c1):
     assert np.abs(z - z1 * z2).max() <= 2.0 ** -10 * max(1.0, np.abs(z1 * z2).max())
 
 
-def test_two_pass_ring_mid_size():
+@pytest.mark.parametrize("crt", [0, 1], ids=["direct_crt", "garner"])
+def test_two_pass_ring_mid_size(crt):
     """N = 2^14 (two-pass NTT), logQ = logP = 438, a batch of two: mult+relin+rescale and a rotation."""
-    P = make_pair(14, 438, 438, seed=14, rot_steps=(5,))
+    P = make_pair(14, 438, 438, seed=14, rot_steps=(5,), crt=crt)
     N = P.prm.N
     la = random_ct_limbs(P.g, 2, N, 438)
     lb = random_ct_limbs(P.g, 2, N, 438)
@@ -158,6 +160,8 @@ def test_two_pass_ring_mid_size():
 @pytest.mark.slow
 def test_full_size_north_star_pair():
     """N = 2^16, logQ = logP = 1200, scale 2^40: one pair, every limb compared with the oracle."""
+    import paper_2607_05920_gb300 as fhe
+
     P = make_pair(16, 1200, 1200, seed=16)
     N = P.prm.N
     la = random_ct_limbs(P.g, 1, N, 1200)
@@ -167,3 +171,7 @@ def test_full_size_north_star_pair():
     want = tuple(ckks.rescale(ckks.mult(_oracle_ct(la)[0], _oracle_ct(lb)[0], P.evk, 1200, 1200), 40, 1200))
     assert got[0] == want
     P.ctx.close()
+    # the Garner reconstruction gives the same ciphertext from the same keys
+    Pg = make_pair(16, 1200, 1200, seed=16, crt=fhe.FHE_CRT_GARNER)
+    assert ct_ints(Pg.ctx.mult_relin_rescale(ca, cb, 40))[0] == want
+    Pg.ctx.close()

@@ -231,15 +231,22 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
 // product: one 32x32->64 multiply-add per (prime, limb), with the constant
 // rows staged in shared memory and read as 128-bit broadcasts.
 template <int LB>
-__global__ void __launch_bounds__(kCrtThreads) k_crt_direct(const uint32_t* __restrict__ in, size_t in_pstride,
-                                                            size_t in_bstride, int r, int npoly,
-                                                            uint32_t* __restrict__ out, size_t out_pstride,
-                                                            size_t out_bstride, EpiArgs epi, int N,
-                                                            const uint32_t* __restrict__ qtab,
-                                                            const uint2* __restrict__ cinv,
-                                                            const uint32_t* __restrict__ qhat,
-                                                            const uint32_t* __restrict__ negm,
-                                                            const float* __restrict__ invq) {
+__global__ void __launch_bounds__(kCrtThreads, (LB <= 64 ? 4 : (LB <= 96 ? 3 : 2))) k_crt_direct(const uint32_t* __restrict__ in, size_t in_pstride,
+                                                               size_t in_bstride, int r, int npoly,
+                                                               uint32_t* __restrict__ out, size_t out_pstride,
+                                                               size_t out_bstride, EpiArgs epi, int N,
+                                                               const uint32_t* __restrict__ qtab,
+                                                               const uint2* __restrict__ cinv,
+                                                               const uint32_t* __restrict__ qhat,
+                                                               const uint32_t* __restrict__ negm,
+                                                               const float* __restrict__ invq) {
+  // The LB limbs are split into NSEG segments with their own carry chains and
+  // 64-bit carry-out counters: the chains are independent within a prime, so
+  // the multiply-adds of different segments overlap; the counters are folded
+  // in once at the end.
+  constexpr int NSEG = (LB % 16 == 0 && LB >= 32) ? 4 : (LB % 8 == 0 && LB >= 16 ? 2 : 1);
+  constexpr int SEG = LB / NSEG;
+  static_assert(SEG % 4 == 0, "segments are read as 128-bit constant vectors");
   extern __shared__ uint32_t sv[];  // first the [r][LB] constant rows, then the [LB+2][T] limb columns
   const int tid = threadIdx.x;
   for (int idx = tid; idx < r * LB; idx += blockDim.x) sv[idx] = __ldg(qhat + (size_t)(idx / LB) * kMaxLimbs + idx % LB);
@@ -252,33 +259,59 @@ __global__ void __launch_bounds__(kCrtThreads) k_crt_direct(const uint32_t* __re
   for (int l = 0; l < LB; ++l) acc[l] = 0;
   if (active) {
     const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
+    uint64_t cout[NSEG];
+#pragma unroll
+    for (int g = 0; g < NSEG; ++g) cout[g] = 0;
     float fs = 0.f;
+    uint32_t x_next = __ldg(src);
+    uint32_t x_next2 = r > 1 ? __ldg(src + N) : 0u;
     for (int i = 0; i < r; ++i) {
-      const uint32_t x = __ldg(src + (size_t)i * N);
+      const uint32_t x = x_next;
+      x_next = x_next2;
+      if (i + 2 < r) x_next2 = __ldg(src + (size_t)(i + 2) * N);  // two primes ahead
       const uint2 ci = __ldg(cinv + i);
       const uint32_t y = shoup_mul(x, ci.x, ci.y, __ldg(qtab + i));
       fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
       const uint4* Q = reinterpret_cast<const uint4*>(sv + i * LB);
-      uint32_t c = 0;
+      uint32_t c[NSEG];
 #pragma unroll
-      for (int l4 = 0; l4 < LB / 4; ++l4) {
-        const uint4 qv = Q[l4];
-        uint64_t t;
-        t = (uint64_t)y * qv.x + acc[4 * l4 + 0]; t += c; acc[4 * l4 + 0] = (uint32_t)t; c = (uint32_t)(t >> 32);
-        t = (uint64_t)y * qv.y + acc[4 * l4 + 1]; t += c; acc[4 * l4 + 1] = (uint32_t)t; c = (uint32_t)(t >> 32);
-        t = (uint64_t)y * qv.z + acc[4 * l4 + 2]; t += c; acc[4 * l4 + 2] = (uint32_t)t; c = (uint32_t)(t >> 32);
-        t = (uint64_t)y * qv.w + acc[4 * l4 + 3]; t += c; acc[4 * l4 + 3] = (uint32_t)t; c = (uint32_t)(t >> 32);
+      for (int g = 0; g < NSEG; ++g) c[g] = 0;
+#pragma unroll
+      for (int l4 = 0; l4 < SEG / 4; ++l4) {
+#pragma unroll
+        for (int g = 0; g < NSEG; ++g) {
+          const int l = g * SEG + 4 * l4;
+          const uint4 qv = Q[l / 4];
+          uint64_t t;
+          t = (uint64_t)y * qv.x + acc[l + 0]; t += c[g]; acc[l + 0] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
+          t = (uint64_t)y * qv.y + acc[l + 1]; t += c[g]; acc[l + 1] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
+          t = (uint64_t)y * qv.z + acc[l + 2]; t += c[g]; acc[l + 2] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
+          t = (uint64_t)y * qv.w + acc[l + 3]; t += c[g]; acc[l + 3] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < NSEG; ++g) cout[g] += c[g];
+    }
+    // fold the segment carries: cout[g] belongs at limb (g + 1) SEG (the last one leaves 2^(32 LB))
+#pragma unroll
+    for (int g = 0; g + 1 < NSEG; ++g) {
+      uint64_t cc = cout[g];
+#pragma unroll
+      for (int l = (g + 1) * SEG; l < LB; ++l) {
+        const uint64_t t = (uint64_t)acc[l] + (uint32_t)cc;
+        acc[l] = (uint32_t)t;
+        cc = (cc >> 32) + (t >> 32);
       }
     }
     // X = acc - kappa M = acc + kappa (-M)  (mod 2^(32 LB))
     const uint32_t kappa = (uint32_t)__float2int_rn(fs);
-    uint32_t c = 0;
+    uint32_t cc = 0;
 #pragma unroll
     for (int l = 0; l < LB; ++l) {
       uint64_t t = (uint64_t)kappa * __ldg(negm + l) + acc[l];
-      t += c;
+      t += cc;
       acc[l] = (uint32_t)t;
-      c = (uint32_t)(t >> 32);
+      cc = (uint32_t)(t >> 32);
     }
   }
   __syncthreads();  // the constant rows are dead: the area becomes the limb columns

@@ -33,9 +33,12 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
                                                        int N, const uint32_t* __restrict__ pow2,
                                                        const uint32_t* __restrict__ qtab,
                                                        const uint32_t* __restrict__ red) {
-  extern __shared__ uint32_t sc[];  // [r][L]
-  for (int idx = threadIdx.x; idx < r * L; idx += blockDim.x)
-    sc[idx] = pow2[(size_t)(idx / L) * kMaxLiftLimbs + (idx % L)];
+  extern __shared__ uint32_t sc[];  // [r][Lp], Lp = L rounded up to 4, zero padded
+  const int Lp = (L + 3) & ~3;
+  for (int idx = threadIdx.x; idx < r * Lp; idx += blockDim.x) {
+    const int i = idx / Lp, l = idx % Lp;
+    sc[idx] = l < L ? pow2[(size_t)i * kMaxLiftLimbs + l] : 0u;
+  }
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
@@ -46,15 +49,18 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
   for (int l = 0; l < LB; ++l) x[l] = (l < L) ? __ldg(s + (size_t)l * N) : 0u;
   uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n;
   for (int i = 0; i < r; ++i) {
-    const uint32_t* c = sc + i * L;
+    const uint4* c4 = reinterpret_cast<const uint4*>(sc + i * Lp);
     uint64_t acc = 0;
     uint32_t a2 = 0;
 #pragma unroll
-    for (int l = 0; l < LB; l += 2) {
-      if (l < L) {
-        // two products < 2^63 each: their sum fits in 64 bits
-        uint64_t p = (uint64_t)x[l] * c[l];
-        if (l + 1 < L) p += (uint64_t)x[l + 1] * c[l + 1];
+    for (int l4 = 0; l4 < LB / 4; ++l4) {
+      if (4 * l4 < L) {
+        // 128-bit broadcast of four constants; two products < 2^63 sum below 2^64
+        const uint4 c = c4[l4];
+        uint64_t p = (uint64_t)x[4 * l4] * c.x + (uint64_t)x[4 * l4 + 1] * c.y;
+        acc += p;
+        a2 += (acc < p);
+        p = (uint64_t)x[4 * l4 + 2] * c.z + (uint64_t)x[4 * l4 + 3] * c.w;
         acc += p;
         a2 += (acc < p);
       }
@@ -88,7 +94,7 @@ static void lift_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t s
   const int N = ctx->N;
   const int threads = N < kLiftThreads ? N : kLiftThreads;
   dim3 grid((N + threads - 1) / threads, npoly * nbatch);
-  size_t smem = (size_t)r * L * sizeof(uint32_t);
+  size_t smem = (size_t)r * ((L + 3) & ~3) * sizeof(uint32_t);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_lift<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_lift<LB><<<grid, threads, smem, st>>>(src, L, sp, sb, dst, dp, db, npoly, r, N, ctx->d_pow2, ctx->d_q,
                                            ctx->d_red);
@@ -102,7 +108,7 @@ int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstri
     set_error("lift: bad sizes L=%d r=%d", L, r);
     return FHE_EINVAL;
   }
-  if ((size_t)r * L * 4 > 200 * 1024) {
+  if ((size_t)r * ((L + 3) & ~3) * 4 > 200 * 1024) {
     set_error("lift: constant table of %d x %d words exceeds 200 KB", r, L);
     return FHE_EINVAL;
   }

@@ -15,14 +15,12 @@
 // only pair elements in the same row, so each pass runs its stages on a tile
 // held in shared memory.  The global twiddle step of the paper is absorbed:
 // in the merged-twist CT network each stage already reads its own twiddle.
-// Rings with N <= 8192 fit one CTA's shared memory and run in one pass.
+// Rings with N <= 4096 run in one CTA (all stages in shared memory).
 #include "common.cuh"
 
 namespace fhe {
 
 constexpr int kRowLen = 256;   // N2
-constexpr int kColTile = 32;   // columns per CTA in the column pass
-constexpr int kRowTile = 4;    // matrix rows per CTA in the row pass
 
 __device__ __forceinline__ void ct_bfly(uint32_t& x, uint32_t& y, uint32_t w, uint32_t wp, uint32_t q) {
   uint32_t v = shoup_mul(y, w, wp, q);
@@ -86,103 +84,220 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
 }
 
 // ------------------------------------------------------------ column pass
-// CTA: kColTile consecutive columns x0.. of one row (poly, prime), N1 x kColTile tile.
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt_cols(uint32_t* __restrict__ data, RowMap rm, int r, int logN, int logN1,
-                                                  const uint32_t* __restrict__ tw, const uint32_t* __restrict__ twp,
-                                                  const uint32_t* __restrict__ qtab,
-                                                  const uint32_t* __restrict__ nscale,
-                                                  const uint32_t* __restrict__ nscale_sh) {
-  extern __shared__ uint32_t s[];  // [N1][kColTile]
-  const int N = 1 << logN, N1 = 1 << logN1;
+// The first log N1 stages of the forward transform (last of the inverse) pair
+// elements in the same column of the N1 x 256 matrix.  A CTA takes 32
+// adjacent columns; each column is split over N1/16 threads that keep 16
+// elements in registers.  Layout A: thread j0 holds rows j0 + (N1/16) k
+// (k < 16), so four stages (row distances N1/2 .. N1/16) run in registers;
+// layout B after one shared-memory exchange: rows 16 j0 + j (j < 16) for
+// the remaining stages (distances N1/32 .. 1).  A warp always spans 32
+// columns of one row: global accesses are 128-byte coalesced, shared-memory
+// accesses conflict-free, and the twiddle of a butterfly depends only on the
+// row, so twiddle loads are warp-wide broadcasts.
+template <int LOGN1>
+__global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+                                                             const uint32_t* __restrict__ tw,
+                                                             const uint32_t* __restrict__ twp,
+                                                             const uint32_t* __restrict__ qtab) {
+  constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
+  __shared__ uint32_t s[N1 * 32];
+  const int col = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+  const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.y, r);
   const uint32_t q = __ldg(qtab + p);
   const uint32_t* w = tw + (size_t)p * N;
   const uint32_t* wp = twp + (size_t)p * N;
-  uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * kColTile;
-  for (int idx = threadIdx.x; idx < N1 * kColTile; idx += blockDim.x) {
-    const int c = idx / kColTile, x = idx % kColTile;
-    s[idx] = a[(size_t)c * kRowLen + x];
+  uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
+  uint32_t x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = a[(size_t)(j0 + TPC * k) * kRowLen];
+  // layout A: distance TPC*h rows, stage index m = 8/h, group k/(2h)
+#pragma unroll
+  for (int h = 8, m = 1; h >= 1; h >>= 1, m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = k / (2 * h);
+      ct_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s[(j0 + TPC * k) * 32 + col] = x[k];
   __syncthreads();
-  const int nb = (N1 >> 1) * kColTile;
-  if (!INV) {
-    for (int m = 1, lt = logN1 - 1; m < N1; m <<= 1, --lt) {
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int x = b % kColTile, bb = b / kColTile;
-        const int i = bb >> lt;
-        const int c = (i << (lt + 1)) + (bb & ((1 << lt) - 1));
-        ct_bfly(s[c * kColTile + x], s[(c + (1 << lt)) * kColTile + x], __ldg(w + m + i), __ldg(wp + m + i), q);
-      }
-      __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < N1 * kColTile; idx += blockDim.x) {
-      const int c = idx / kColTile, x = idx % kColTile;
-      a[(size_t)c * kRowLen + x] = s[idx];
-    }
-  } else {
-    for (int h = N1 >> 1, lt = 0; h >= 1; h >>= 1, ++lt) {
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int x = b % kColTile, bb = b / kColTile;
-        const int i = bb >> lt;
-        const int c = (i << (lt + 1)) + (bb & ((1 << lt) - 1));
-        gs_bfly(s[c * kColTile + x], s[(c + (1 << lt)) * kColTile + x], __ldg(w + h + i), __ldg(wp + h + i), q);
-      }
-      __syncthreads();
-    }
-    const uint32_t sc = __ldg(nscale + p), scp = __ldg(nscale_sh + p);
-    for (int idx = threadIdx.x; idx < N1 * kColTile; idx += blockDim.x) {
-      const int c = idx / kColTile, x = idx % kColTile;
-      a[(size_t)c * kRowLen + x] = shoup_mul(s[idx], sc, scp, q);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = s[(16 * j0 + j) * 32 + col];
+  // layout B: distance h rows (h = N1/32 .. 1), stage index N1/(2h), group (16 j0 + j)/(2h)
+#pragma unroll
+  for (int h = N1 / 32; h >= 1; h >>= 1) {
+    const int m = N1 / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = j0 * (8 / h) + j / (2 * h);
+      ct_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
     }
   }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[(size_t)(16 * j0 + j) * kRowLen] = x[j];
+}
+
+template <int LOGN1>
+__global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+                                                             const uint32_t* __restrict__ tw,
+                                                             const uint32_t* __restrict__ twp,
+                                                             const uint32_t* __restrict__ qtab,
+                                                             const uint32_t* __restrict__ nscale,
+                                                             const uint32_t* __restrict__ nscale_sh) {
+  constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
+  __shared__ uint32_t s[N1 * 32];
+  const int col = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+  const int N = 1 << logN;
+  const int p = rm.prime_of(blockIdx.y, r);
+  const uint32_t q = __ldg(qtab + p);
+  const uint32_t* w = tw + (size_t)p * N;
+  const uint32_t* wp = twp + (size_t)p * N;
+  uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
+  uint32_t x[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = a[(size_t)(16 * j0 + j) * kRowLen];
+#pragma unroll
+  for (int h = 1; h <= N1 / 32; h <<= 1) {
+    const int m = N1 / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = j0 * (8 / h) + j / (2 * h);
+      gs_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s[(16 * j0 + j) * 32 + col] = x[j];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = s[(j0 + TPC * k) * 32 + col];
+#pragma unroll
+  for (int h = 1, m = 8; h <= 8; h <<= 1, m >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = k / (2 * h);
+      gs_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
+  }
+  const uint32_t sc = __ldg(nscale + p), scp = __ldg(nscale_sh + p);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[(size_t)(j0 + TPC * k) * kRowLen] = shoup_mul(x[k], sc, scp, q);
 }
 
 // --------------------------------------------------------------- row pass
-// CTA: kRowTile consecutive matrix rows c0.. of kRowLen contiguous words.
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt_rows(uint32_t* __restrict__ data, RowMap rm, int r, int logN, int logN1,
-                                                  const uint32_t* __restrict__ tw,
-                                                  const uint32_t* __restrict__ twp,
-                                                  const uint32_t* __restrict__ qtab) {
-  __shared__ uint32_t s[kRowTile * kRowLen];
-  const int N = 1 << logN, N1 = 1 << logN1;
+// The last 8 stages of the forward transform (first of the inverse) stay in
+// one 256-word matrix row.  16 threads per row, 8 rows per CTA.  Layout A:
+// thread j0 holds j0 + 16 k (distances 128 .. 16); layout B after a padded
+// shared-memory exchange: 16 j0 + j (distances 8 .. 1), stored as four
+// 128-bit writes.
+constexpr int kRowsPerCta = 8;
+__device__ __forceinline__ int rpad(int pos) { return pos + (pos >> 4); }
+
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __restrict__ data, RowMap rm, int r,
+                                                                   int logN, const uint32_t* __restrict__ tw,
+                                                                   const uint32_t* __restrict__ twp,
+                                                                   const uint32_t* __restrict__ qtab) {
+  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.y, r);
   const uint32_t q = __ldg(qtab + p);
   const uint32_t* w = tw + (size_t)p * N;
   const uint32_t* wp = twp + (size_t)p * N;
-  const int c0 = blockIdx.x * kRowTile;
-  uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c0 * kRowLen;
-  for (int idx = threadIdx.x; idx < kRowTile * kRowLen; idx += blockDim.x) s[idx] = a[idx];
-  __syncthreads();
-  constexpr int kHalf = kRowLen / 2;
-  constexpr int nb = kRowTile * kHalf;
-  if (!INV) {
-    // stages m = N1 .. N/2, t = kRowLen/2 .. 1
-    for (int m = N1, lt = 7; lt >= 0; m <<= 1, --lt) {
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int cr = b / kHalf, bj = b % kHalf;
-        const int il = bj >> lt;
-        const int jl = (il << (lt + 1)) + (bj & ((1 << lt) - 1));
-        const int i = ((c0 + cr) << (7 - lt)) + il;  // global butterfly group
-        ct_bfly(s[cr * kRowLen + jl], s[cr * kRowLen + jl + (1 << lt)], __ldg(w + m + i), __ldg(wp + m + i), q);
-      }
-      __syncthreads();
-    }
-  } else {
-    // stages t = 1 .. kRowLen/2, h = N/2 .. N1
-    for (int h = N >> 1, lt = 0; lt <= 7; h >>= 1, ++lt) {
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int cr = b / kHalf, bj = b % kHalf;
-        const int il = bj >> lt;
-        const int jl = (il << (lt + 1)) + (bj & ((1 << lt) - 1));
-        const int i = ((c0 + cr) << (7 - lt)) + il;
-        gs_bfly(s[cr * kRowLen + jl], s[cr * kRowLen + jl + (1 << lt)], __ldg(w + h + i), __ldg(wp + h + i), q);
-      }
-      __syncthreads();
+  const int c = blockIdx.x * kRowsPerCta + sub;  // matrix row
+  uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c * kRowLen;
+  uint32_t* sr = s + sub * (kRowLen + kRowLen / 16);
+  uint32_t x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
+  // layout A: distance t = 16 h, stage index N/(2t), group c (8/h) + k/(2h)
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const int m = N / (32 * h);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = c * (8 / h) + k / (2 * h);
+      ct_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
     }
   }
-  for (int idx = threadIdx.x; idx < kRowTile * kRowLen; idx += blockDim.x) a[idx] = s[idx];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sr[rpad(j0 + 16 * k)] = x[k];
+  __syncwarp();  // a row's 16 threads are half of one warp
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = sr[rpad(16 * j0 + j)];
+  // layout B: distance t = h, stage index N/(2h), group c (128/h) + j0 (8/h) + j/(2h)
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const int m = N / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
+      ct_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
+  }
+  uint4* a4 = reinterpret_cast<uint4*>(a + 16 * j0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) a4[v] = make_uint4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+}
+
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __restrict__ data, RowMap rm, int r,
+                                                                   int logN, const uint32_t* __restrict__ tw,
+                                                                   const uint32_t* __restrict__ twp,
+                                                                   const uint32_t* __restrict__ qtab) {
+  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int p = rm.prime_of(blockIdx.y, r);
+  const uint32_t q = __ldg(qtab + p);
+  const uint32_t* w = tw + (size_t)p * N;
+  const uint32_t* wp = twp + (size_t)p * N;
+  const int c = blockIdx.x * kRowsPerCta + sub;
+  uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c * kRowLen;
+  uint32_t* sr = s + sub * (kRowLen + kRowLen / 16);
+  uint32_t x[16];
+  const uint4* a4 = reinterpret_cast<const uint4*>(a + 16 * j0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 t = a4[v];
+    x[4 * v] = t.x;
+    x[4 * v + 1] = t.y;
+    x[4 * v + 2] = t.z;
+    x[4 * v + 3] = t.w;
+  }
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1) {
+    const int m = N / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
+      gs_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sr[rpad(16 * j0 + j)] = x[j];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = sr[rpad(j0 + 16 * k)];
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1) {
+    const int m = N / (32 * h);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = c * (8 / h) + k / (2 * h);
+      gs_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[j0 + 16 * k] = x[k];
 }
 
 static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
@@ -190,8 +305,8 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
   const int logN = ctx->prm.logN, N = ctx->N;
   const uint32_t* tw = inverse ? ctx->d_ipsi : ctx->d_psi;
   const uint32_t* twp = inverse ? ctx->d_ipsi_sh : ctx->d_psi_sh;
-  ProfScope ps(ctx, inverse ? FHE_K_NTT_INV : FHE_K_NTT_FWD, logN <= 13 ? 1 : 2, st);
-  if (logN <= 13) {
+  ProfScope ps(ctx, inverse ? FHE_K_NTT_INV : FHE_K_NTT_FWD, logN <= 12 ? 1 : 2, st);
+  if (logN <= 12) {
     const int threads = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
     const size_t smem = (size_t)N * 4;
     if (inverse)
@@ -203,17 +318,23 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
     return FHE_OK;
   }
   const int logN1 = logN - 8, N1 = 1 << logN1;
-  const size_t csmem = (size_t)N1 * kColTile * 4;
-  dim3 gcols(kRowLen / kColTile, rows), grows(N1 / kRowTile, rows);
+  dim3 gcols(kRowLen / 32, rows), grows(N1 / kRowsPerCta, rows);
+#define FHE_NTT_COLS(L)                                                                                    \
+  case L:                                                                                                  \
+    if (inverse)                                                                                           \
+      k_ntt_cols_inv<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q, ctx->d_nscale,     \
+                                                  ctx->d_nscale_sh);                                       \
+    else                                                                                                   \
+      k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);                   \
+    break;
   if (!inverse) {
-    k_ntt_cols<false><<<gcols, 256, csmem, st>>>(data, rm, r, logN, logN1, tw, twp, ctx->d_q, ctx->d_nscale,
-                                                  ctx->d_nscale_sh);
-    k_ntt_rows<false><<<grows, 256, 0, st>>>(data, rm, r, logN, logN1, tw, twp, ctx->d_q);
+    switch (logN1) { FHE_NTT_COLS(5) FHE_NTT_COLS(6) FHE_NTT_COLS(7) FHE_NTT_COLS(8) }
+    k_ntt_rows_fwd<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);
   } else {
-    k_ntt_rows<true><<<grows, 256, 0, st>>>(data, rm, r, logN, logN1, tw, twp, ctx->d_q);
-    k_ntt_cols<true><<<gcols, 256, csmem, st>>>(data, rm, r, logN, logN1, tw, twp, ctx->d_q, ctx->d_nscale,
-                                                 ctx->d_nscale_sh);
+    k_ntt_rows_inv<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);
+    switch (logN1) { FHE_NTT_COLS(5) FHE_NTT_COLS(6) FHE_NTT_COLS(7) FHE_NTT_COLS(8) }
   }
+#undef FHE_NTT_COLS
   return FHE_OK;
 }
 

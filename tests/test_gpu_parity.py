@@ -51,6 +51,26 @@ def test_ring_mul_matches_exact_product(logN, La, Lb, logOut, crt):
     ctx.close()
 
 
+@pytest.mark.parametrize("crt", [0, 1], ids=["direct_crt", "garner"])
+def test_ring_mul_every_limb_bucket(crt):
+    """Outputs of 8 .. 128 limbs (every register bucket of the reconstruction), products wider than the output."""
+    import paper_2607_05920_gb300 as fhe
+
+    logN = 8
+    N = 1 << logN
+    ctx = fhe.Context(logN, 2000, 1900, crt=crt)
+    g = fs.rng(88 + crt)
+    for out_limbs in (8, 13, 16, 24, 32, 38, 40, 48, 56, 64, 75, 80, 96, 112, 128):
+        logOut = 32 * out_limbs - 5
+        La = out_limbs // 2 + 1
+        a = fs.uniform_limbs(g, (1,), N, 32 * La)
+        b = fs.uniform_limbs(g, (1,), N, 32 * La - 7)
+        out = ctx.ring_mul(to_dev(a), to_dev(b), logOut).cpu().numpy().view(np.uint32)
+        want = ring.negacyclic_fast(bigint.from_limbs(a[0]), bigint.from_limbs(b[0]))
+        assert bigint.from_limbs(out[0]) == [x % (1 << logOut) for x in want], out_limbs
+    ctx.close()
+
+
 @pytest.fixture(scope="module", params=[0, 1], ids=["direct_crt", "garner"])
 def c1(request):
     # N = 2^11, Q = P = 2^120 (the smallest workload), plus rotation keys; both reconstructions

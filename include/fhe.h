@@ -58,6 +58,7 @@ extern "C" {
 #define FHE_EWORKSPACE (-7)/* workspace null, too small or misaligned              */
 
 #define FHE_SCHEME_CKKS 0
+#define FHE_SCHEME_BGV 1
 
 /* Operation codes for fhe_workspace_bytes. */
 #define FHE_OP_MULT 1      /* fhe_mult_relin / fhe_mult_relin_rescale  */
@@ -76,13 +77,18 @@ typedef void* (*fhe_alloc_fn)(size_t bytes, void* user);
 typedef void (*fhe_free_fn)(void* ptr, size_t bytes, void* user);
 
 typedef struct {
-  int32_t scheme; /* FHE_SCHEME_CKKS                                                  */
+  int32_t scheme; /* FHE_SCHEME_CKKS or FHE_SCHEME_BGV                                */
   int32_t logN;   /* ring X^N + 1, N = 2^logN, 3 <= logN <= 16 (Sec. 6 parameter n)   */
-  int32_t logQ;   /* top ciphertext modulus Q = 2^logQ, 1 <= logQ <= 3200 (Sec. 6)     */
-  int32_t logP;   /* special modulus P = 2^logP of the switching keys, 1..3200        */
+  int32_t logQ;   /* CKKS: top modulus Q = 2^logQ (Sec. 6 log q).  BGV: the bit length
+                     of the top modulus Q_L = q0 r^L (checked)                         */
+  int32_t logP;   /* special modulus P = 2^logP of the switching keys                 */
   int32_t crt;    /* RNS -> limb reconstruction: FHE_CRT_DIRECT (0, default) or
                      FHE_CRT_GARNER (1, the mixed-radix form of Sec. 2 Eq. garner_mrc);
                      both give identical results                                    */
+  int32_t bgv_levels; /* BGV: top level L of the chain Q_l = q0 r^l (0 for CKKS)      */
+  uint32_t t;         /* BGV: plaintext modulus, odd, 3 <= t < 2^31 (0 for CKKS)      */
+  uint64_t bgv_q0;    /* BGV: odd, = 1 mod t                                         */
+  uint64_t bgv_r;     /* BGV: odd, = 1 mod t, 2^8 < r < 2^62                           */
 } fhe_params;
 
 #define FHE_CRT_DIRECT 0 /* exact CRT sum with a rounded quotient (Halevi-Polyakov-Shoup) */
@@ -91,7 +97,9 @@ typedef struct {
 typedef struct {
   uint32_t* data; /* device, uint32_t[cnum][2][L][N], L = ceil(logQ/32)               */
   int32_t cnum;   /* batch size (CipherTensor cnum, Sec. 6)                          */
-  int32_t logQ;   /* this ciphertext's modulus 2^logQ (its level), <= the top logQ   */
+  int32_t logQ;   /* CKKS: this ciphertext's modulus 2^logQ (its level), <= the top.
+                     BGV: the bit length of Q_level (must match `level`)             */
+  int32_t level;  /* BGV: level l of the modulus Q_l = q0 r^l (ignored for CKKS)     */
 } fhe_ct;
 
 /* Create a context for one ring size and modulus chain.  Computes the NTT
@@ -121,6 +129,8 @@ size_t fhe_ct_bytes(int logN, int logQ, int cnum);
 size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum);
 
 /* Key generation (Sec. 6 "Cryptographic Key Management": sk, pk, rk).
+ * BGV: the errors are multiplied by t, Q is the top chain modulus q0 r^L and
+ * a_pk / a_ev are first reduced modulo Q and P Q (any limbs are accepted).
  * All random polynomials are supplied by the caller (host pointers), so that
  * results are reproducible:
  *   s     int8_t[N]            secret, coefficients in {-1, 0, 1}
@@ -141,7 +151,9 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
 int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e);
 
 /* Public-key encryption (encrypt_pairwise_upon, Sec. 6) of cnum plaintexts:
- *   out = (v pk_b + m + e0, v pk_a + e1) mod 2^out->logQ
+ *   CKKS: out = (v pk_b + m + e0, v pk_a + e1) mod 2^out->logQ
+ *   BGV:  out = (v pk_b + m + t e0, v pk_a + t e1) mod Q_{out->level}, pt canonical
+ *         residues (m in [0, t) in limb 0)
  * pt: device uint32_t[cnum][L][N], each coefficient m mod 2^logQ (a signed
  * plaintext in two's complement); v: device int8_t[cnum][N] in {-1,0,1};
  * e0, e1: device int32_t[cnum][N].  out->data, out->cnum, out->logQ set by
@@ -150,11 +162,15 @@ int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t
                 fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
 
 /* Decryption (decrypt_pairwise_upon, Sec. 6): m = [b + a s]_Q with the centred
- * reduction of Sec. 5 ("if x > Q/2, x <- x - Q"), written as L-limb two's
- * complement (sign-extended to 32 L bits).  pt_out: device uint32_t[cnum][L][N]. */
+ * reduction of Sec. 5 ("if x > Q/2, x <- x - Q").  CKKS: written as L-limb two's
+ * complement (sign-extended to 32 L bits), pt_out device uint32_t[cnum][L][N].
+ * BGV: m mod t of the centred value, pt_out device uint32_t[cnum][N]. */
 int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size_t ws_bytes, void* stream);
 
-/* Homomorphic multiplication with relinearisation (mult_pairwise_into, Sec. 6):
+/* Homomorphic multiplication with relinearisation (mult_pairwise_into, Sec. 6).
+ * BGV: same shape modulo the odd Q_l of the operands' level, with the key-switch
+ * division (y + delta)/P, delta = t [(-y) t^-1]_P (centred), so delta = 0 mod t.
+ * CKKS:
  *   (d0, d1, d2) = (b1 b2, a1 b2 + a2 b1, a1 a2) mod Q    (Karatsuba, Sec. 5)
  *   out = (d0, d1) + round(P^-1 (d2 evk_b, d2 evk_a) mod P Q)  (mod Q)
  * a, b: same cnum and logQ; out: same cnum and logQ, must not alias a or b. */
@@ -170,8 +186,10 @@ int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k
  * 2^(logQ - k), halves rounded up; out->logQ must equal in->logQ - k. */
 int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream);
 
-/* Modulus drop (moddownBy_pairwise_into, Sec. 6): out = in mod 2^out->logQ,
- * out->logQ <= in->logQ (scale unchanged). */
+/* Modulus drop (moddownBy_pairwise_into, Sec. 6).  CKKS: out = in mod
+ * 2^out->logQ, out->logQ <= in->logQ (scale unchanged).  BGV: the modulus
+ * switch Q_l -> Q_{l-1} = Q_l / r, c' = (c + t [(-c) t^-1]_r) / r (centred),
+ * out->level = in->level - 1, no aliasing. */
 int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
 
 /* Left rotation by `step` slots (leftrotate_broadcast_into, Sec. 6):

@@ -34,6 +34,7 @@ FHE_ECUDA = -5
 FHE_ETIMEOUT = -6
 FHE_EWORKSPACE = -7
 FHE_SCHEME_CKKS = 0
+FHE_SCHEME_BGV = 1
 FHE_CRT_DIRECT = 0
 FHE_CRT_GARNER = 1
 FHE_OP_MULT = 1
@@ -46,11 +47,13 @@ FHE_OP_RING_MUL = 6
 
 class FheParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("logN", ctypes.c_int32), ("logQ", ctypes.c_int32),
-                ("logP", ctypes.c_int32), ("crt", ctypes.c_int32)]
+                ("logP", ctypes.c_int32), ("crt", ctypes.c_int32), ("bgv_levels", ctypes.c_int32),
+                ("t", ctypes.c_uint32), ("bgv_q0", ctypes.c_uint64), ("bgv_r", ctypes.c_uint64)]
 
 
 class FheCt(ctypes.Structure):
-    _fields_ = [("data", ctypes.c_void_p), ("cnum", ctypes.c_int32), ("logQ", ctypes.c_int32)]
+    _fields_ = [("data", ctypes.c_void_p), ("cnum", ctypes.c_int32), ("logQ", ctypes.c_int32),
+                ("level", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -125,17 +128,21 @@ def limbs(bits: int) -> int:
 
 @dataclass
 class Ciphertext:
-    """A CipherTensor: data (cnum, 2, L, N) int32 CUDA tensor of uint32 limbs at modulus 2^logQ."""
+    """A CipherTensor: data (cnum, 2, L, N) int32 CUDA tensor of uint32 limbs.
+
+    CKKS: modulus 2^logQ.  BGV: modulus Q_level = q0 r^level of logQ bits.
+    """
 
     data: "object"
     logQ: int
+    level: int = 0
 
     @property
     def cnum(self) -> int:
         return int(self.data.shape[0])
 
     def c(self) -> FheCt:
-        return FheCt(self.data.data_ptr(), self.cnum, self.logQ)
+        return FheCt(self.data.data_ptr(), self.cnum, self.logQ, self.level)
 
 
 def _stream():
@@ -152,7 +159,8 @@ def _host(arr, dtype) -> np.ndarray:
 class Context:
     """One ring size and modulus chain; owns tables and keys (allocated through torch)."""
 
-    def __init__(self, logN: int, logQ: int, logP: int, crt: int = FHE_CRT_DIRECT):
+    def __init__(self, logN: int, logQ: int, logP: int, crt: int = FHE_CRT_DIRECT, scheme: int = FHE_SCHEME_CKKS,
+                 t: int = 0, bgv_q0: int = 0, bgv_r: int = 0, bgv_levels: int = 0):
         import torch
 
         self.logN, self.logQ, self.logP = int(logN), int(logQ), int(logP)
@@ -171,8 +179,11 @@ class Context:
 
         self._alloc_cb = ALLOC_FN(_alloc)
         self._free_cb = FREE_FN(_free)
-        prm = FheParams(FHE_SCHEME_CKKS, self.logN, self.logQ, self.logP, int(crt))
+        prm = FheParams(int(scheme), self.logN, self.logQ, self.logP, int(crt), int(bgv_levels), int(t), int(bgv_q0),
+                        int(bgv_r))
         self.crt = int(crt)
+        self.scheme = int(scheme)
+        self.t, self.bgv_q0, self.bgv_r, self.bgv_levels = int(t), int(bgv_q0), int(bgv_r), int(bgv_levels)
         h = ctypes.c_void_p()
         _check(lib.fhe_ctx_create(ctypes.byref(prm), self._alloc_cb, self._free_cb, None, ctypes.byref(h)),
                "fhe_ctx_create")
@@ -202,9 +213,17 @@ class Context:
             self._ws[op] = cur
         return cur
 
-    def empty_ct(self, cnum: int, logQ: int) -> Ciphertext:
+    def bgv_bits(self, level: int) -> int:
+        """Bit length of Q_level = q0 r^level (BGV)."""
+        return (self.bgv_q0 * self.bgv_r ** int(level)).bit_length()
+
+    def empty_ct(self, cnum: int, logQ: int, level: int = 0) -> Ciphertext:
         t = self._torch.empty((int(cnum), 2, limbs(logQ), self.N), dtype=self._torch.int32, device=self.device)
-        return Ciphertext(t, int(logQ))
+        return Ciphertext(t, int(logQ), int(level))
+
+    def empty_level(self, cnum: int, level: int) -> Ciphertext:
+        """An uninitialised BGV ciphertext batch at `level`."""
+        return self.empty_ct(cnum, self.bgv_bits(level), level)
 
     # ------------------------------------------------------------------ keys
     def keygen(self, s, a_pk, e_pk, a_ev, e_ev) -> None:
@@ -214,19 +233,33 @@ class Context:
         fhe_keygen_rotation(self, step, a, e)
 
     # ------------------------------------------------------------ operations
-    def encrypt(self, pt, v, e0, e1, logQ: int | None = None) -> Ciphertext:
-        out = self.empty_ct(pt.shape[0], self.logQ if logQ is None else logQ)
+    def encrypt(self, pt, v, e0, e1, logQ: int | None = None, level: int | None = None) -> Ciphertext:
+        if self.scheme == FHE_SCHEME_BGV:
+            lv = self.bgv_levels if level is None else int(level)
+            out = self.empty_level(pt.shape[0], lv)
+        else:
+            out = self.empty_ct(pt.shape[0], self.logQ if logQ is None else logQ)
         fhe_encrypt(self, pt, v, e0, e1, out)
         return out
 
     def decrypt(self, ct: Ciphertext):
-        out = self._torch.empty((ct.cnum, limbs(ct.logQ), self.N), dtype=self._torch.int32, device=self.device)
+        """CKKS: (cnum, L, N) centred two's-complement limbs.  BGV: (cnum, N) plaintext coefficients mod t."""
+        if self.scheme == FHE_SCHEME_BGV:
+            out = self._torch.empty((ct.cnum, self.N), dtype=self._torch.int32, device=self.device)
+        else:
+            out = self._torch.empty((ct.cnum, limbs(ct.logQ), self.N), dtype=self._torch.int32, device=self.device)
         fhe_decrypt(self, ct, out)
         return out
 
     def mult_relin(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
-        out = self.empty_ct(a.cnum, a.logQ)
+        out = self.empty_ct(a.cnum, a.logQ, a.level)
         fhe_mult_relin(self, a, b, out)
+        return out
+
+    def mod_switch(self, ct: Ciphertext) -> Ciphertext:
+        """BGV modulus switch to level - 1 (fhe_moddown)."""
+        out = self.empty_level(ct.cnum, ct.level - 1)
+        fhe_moddown(self, ct, out)
         return out
 
     def mult_relin_rescale(self, a: Ciphertext, b: Ciphertext, k: int) -> Ciphertext:
@@ -250,17 +283,17 @@ class Context:
         return out
 
     def add(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
-        out = self.empty_ct(a.cnum, a.logQ)
+        out = self.empty_ct(a.cnum, a.logQ, a.level)
         fhe_add(self, a, b, out)
         return out
 
     def sub(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
-        out = self.empty_ct(a.cnum, a.logQ)
+        out = self.empty_ct(a.cnum, a.logQ, a.level)
         fhe_sub(self, a, b, out)
         return out
 
     def negate(self, a: Ciphertext) -> Ciphertext:
-        out = self.empty_ct(a.cnum, a.logQ)
+        out = self.empty_ct(a.cnum, a.logQ, a.level)
         fhe_negate(self, a, out)
         return out
 
@@ -319,8 +352,9 @@ def fhe_decrypt(ctx: Context, ct: Ciphertext, out) -> None:
 
     ws = ctx.workspace(FHE_OP_DECRYPT, ct.logQ, ct.cnum)
     c = ct.c()
-    _check(lib.fhe_decrypt(ctx.handle, ctypes.byref(c), _dev(out, torch.int32, (ct.cnum, limbs(ct.logQ), ctx.N)),
-                           ws.data_ptr(), ws.numel(), _stream()), "fhe_decrypt")
+    shape = (ct.cnum, ctx.N) if ctx.scheme == FHE_SCHEME_BGV else (ct.cnum, limbs(ct.logQ), ctx.N)
+    _check(lib.fhe_decrypt(ctx.handle, ctypes.byref(c), _dev(out, torch.int32, shape), ws.data_ptr(), ws.numel(),
+                           _stream()), "fhe_decrypt")
 
 
 def fhe_mult_relin(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:

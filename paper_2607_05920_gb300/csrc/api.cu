@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include "bgv.cuh"
 #include "common.cuh"
 
 using namespace fhe;
@@ -84,8 +85,28 @@ size_t words_ringmul(const fhe_ctx* c, int bits, int cnum) {
   return (size_t)cnum * c->N * 2 * (size_t)r + 2 * 64;
 }
 
+bool is_bgv(const fhe_ctx* ctx) { return ctx->prm.scheme == FHE_SCHEME_BGV; }
+
 bool ct_ok(const fhe_ctx* ctx, const fhe_ct* ct) {
-  return ct && ct->data && ct->cnum >= 1 && ct->cnum <= kMaxCnum && ct->logQ >= 1 && ct->logQ <= ctx->prm.logQ;
+  if (!ct || !ct->data || ct->cnum < 1 || ct->cnum > kMaxCnum || ct->logQ < 1 || ct->logQ > ctx->prm.logQ) return false;
+  if (is_bgv(ctx))
+    return ct->level >= 0 && ct->level <= ctx->prm.bgv_levels && ct->logQ == ctx->bgv_bits[ct->level];
+  return true;
+}
+
+// BGV: limbs of the exact signed product emitted by the CRT (bound + sign + headroom)
+int bgv_prod_limbs(int bound_bits) { return limbs_for_bits(bound_bits + 2); }
+
+size_t words_mult_bgv(const fhe_ctx* c, int bits, int cnum) {
+  const size_t N = c->N;
+  const int rt = r_tensor(c, bits), rk = r_keyswitch(c, bits), L = limbs_for_bits(bits);
+  if (rt < 0 || rk < 0) return 0;
+  const int nxt = bgv_prod_limbs(c->prm.logN + 2 * bits + 1);
+  const int nxk = bgv_prod_limbs(c->prm.logN + bits + c->prm.logP + c->prm.logQ);
+  const int nz = nxk - (c->prm.logP >> 5);
+  return (size_t)cnum * N *
+             (4 * (size_t)rt + 3 * (size_t)nxt + 3 * (size_t)L + 2 * (size_t)rk + 2 * (size_t)nxk + 2 * (size_t)nz) +
+         6 * 64;
 }
 
 // One ring product C = A * B into limbs through `epi`.  A: La limbs or small
@@ -158,6 +179,59 @@ int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int n
   return check_launch();
 }
 
+// BGV multiplication at level l: exact tensor product reduced mod Q_l, then the
+// key switch (d2 evk, divided by P with the t-multiple correction) added to (d0, d1).
+int mult_bgv(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* ws, size_t ws_bytes,
+             cudaStream_t st) {
+  const int bits = a->logQ, level = a->level, cnum = a->cnum, L = limbs_for_bits(bits);
+  const int rt = r_tensor(ctx, bits), rk = r_keyswitch(ctx, bits);
+  const int nxt = bgv_prod_limbs(ctx->prm.logN + 2 * bits + 1);
+  const int nxk = bgv_prod_limbs(ctx->prm.logN + bits + ctx->prm.logP + ctx->prm.logQ);
+  const int nz = nxk - (ctx->prm.logP >> 5);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* X = cv.take((size_t)cnum * 4 * rt * N);
+  uint32_t* T1 = cv.take((size_t)cnum * 3 * nxt * N);
+  uint32_t* D = cv.take((size_t)cnum * 3 * L * N);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
+  uint32_t* T2 = cv.take((size_t)cnum * 2 * nxk * N);
+  uint32_t* Z = cv.take((size_t)cnum * 2 * nz * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("mult (BGV): workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  const size_t ctw = 2 * (size_t)L * N;
+  RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
+  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
+                     4 * (size_t)rt * N, 2, cnum, rt, st));
+  RET_IF(launch_ntt(ctx, X, cnum * 4, rt, rt, rt, false, st));
+  RET_IF(launch_pointwise_tensor(ctx, X, rt, cnum, st));
+  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  EpiArgs e0;
+  e0.kind = Epi::kStore;
+  e0.out_bits = 32 * nxt;
+  e0.out_limbs = nxt;
+  RET_IF(launch_garner(ctx, X, (size_t)rt * N, 4 * (size_t)rt * N, rt, 3, cnum, T1, (size_t)nxt * N,
+                       3 * (size_t)nxt * N, e0, st));
+  RET_IF(launch_bgv_reduce(ctx, T1, nxt, (size_t)nxt * N, 3 * (size_t)nxt * N, 3, cnum, true, false, nullptr, nullptr,
+                           0, nullptr, 0, 0, 0, D, (size_t)L * N, 3 * (size_t)L * N, level, st));
+  RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
+                     st));
+  RET_IF(launch_ntt(ctx, Y, cnum, rk, 2 * rk, rk, false, st));
+  RET_IF(launch_pointwise_key(ctx, Y, ctx->evk.ntt, ctx->evk.rows, rk, cnum, st));
+  RET_IF(launch_ntt(ctx, Y, cnum * 2, rk, rk, rk, true, st));
+  EpiArgs e1;
+  e1.kind = Epi::kStore;
+  e1.out_bits = 32 * nxk;
+  e1.out_limbs = nxk;
+  RET_IF(launch_garner(ctx, Y, (size_t)rk * N, 2 * (size_t)rk * N, rk, 2, cnum, T2, (size_t)nxk * N,
+                       2 * (size_t)nxk * N, e1, st));
+  RET_IF(launch_bgv_keyswitch(ctx, T2, nxk, (size_t)nxk * N, 2 * (size_t)nxk * N, D, 2, (size_t)L * N,
+                              3 * (size_t)L * N, out->data, (size_t)L * N, 2 * (size_t)L * N, cnum, level, Z,
+                              (size_t)nz * N, 2 * (size_t)nz * N, st));
+  return check_launch();
+}
+
 int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* out, void* ws, size_t ws_bytes,
               void* stream) {
   if (!ctx || !ct_ok(ctx, a) || !ct_ok(ctx, b) || !ct_ok(ctx, out)) {
@@ -179,6 +253,13 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
   if (out->data == a->data || out->data == b->data) {
     set_error("mult: out aliases an input");
     return FHE_EINVAL;
+  }
+  if (is_bgv(ctx)) {
+    if (k2 != 0 || a->level != b->level || out->level != a->level) {
+      set_error("mult (BGV): operands and output must share one level; no rescale");
+      return FHE_ELEVEL;
+    }
+    return mult_bgv(ctx, a, b, out, ws, ws_bytes, (cudaStream_t)stream);
   }
   const int logQ = a->logQ, cnum = a->cnum, L = limbs_for_bits(logQ);
   const int rt = r_tensor(ctx, logQ), rk = r_keyswitch(ctx, logQ);
@@ -260,11 +341,22 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
     return FHE_EINVAL;
   }
   *out = nullptr;
-  if (p->scheme != FHE_SCHEME_CKKS || p->logN < 3 || p->logN > kMaxLogN || p->logQ < 1 || p->logP < 1 ||
+  if ((p->scheme != FHE_SCHEME_CKKS && p->scheme != FHE_SCHEME_BGV) || p->logN < 3 || p->logN > kMaxLogN ||
+      p->logQ < 1 || p->logP < 1 ||
       p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr) ||
       (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER)) {
     set_error("ctx_create: parameters out of range (logN %d, logQ %d, logP %d)", p->logN, p->logQ, p->logP);
     return FHE_EINVAL;
+  }
+  if (p->scheme == FHE_SCHEME_BGV) {
+    const bool ok = p->t >= 3 && (p->t & 1u) && p->t < (1u << 31) && p->bgv_levels >= 1 && p->bgv_levels <= 64 &&
+                    (p->bgv_q0 & 1u) && (p->bgv_r & 1u) && p->bgv_q0 % p->t == 1 % p->t && p->bgv_r % p->t == 1 % p->t &&
+                    p->bgv_q0 > p->t && p->bgv_r > 256 && p->bgv_r < ((uint64_t)1 << 62) && p->logP < 32 * kBgvLimbs &&
+                    p->logP >= p->logQ;
+    if (!ok) {
+      set_error("ctx_create: BGV chain parameters out of range (t odd, q0 = r = 1 mod t, odd, logP >= logQ)");
+      return FHE_EINVAL;
+    }
   }
   const int R = primes_for_bound_global(p->logN + 2 * p->logQ + p->logP);
   if (R < 0) {
@@ -281,6 +373,13 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   ctx->crt_mode = p->crt;
   cudaGetDevice(&ctx->device);
   int rc = build_tables(ctx);
+  if (rc == FHE_OK && p->scheme == FHE_SCHEME_BGV) {
+    rc = build_bgv_tables(ctx);
+    if (rc == FHE_OK && ctx->bgv_bits[p->bgv_levels] != p->logQ) {
+      set_error("ctx_create: logQ = %d but q0 r^L has %d bits", p->logQ, ctx->bgv_bits[p->bgv_levels]);
+      rc = FHE_EINVAL;
+    }
+  }
   if (rc != FHE_OK) {
     free_all(ctx);
     delete ctx;
@@ -311,7 +410,7 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
   switch (op) {
     case FHE_OP_MULT:
       if (logQ > ctx->prm.logQ) return 0;
-      w = words_mult(ctx, logQ, cnum);
+      w = is_bgv(ctx) ? words_mult_bgv(ctx, logQ, cnum) : words_mult(ctx, logQ, cnum);
       break;
     case FHE_OP_ROTATE:
       if (logQ > ctx->prm.logQ) return 0;
@@ -319,10 +418,13 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
       break;
     case FHE_OP_ENCRYPT:
       w = words_encrypt(ctx, cnum);
+      if (w && is_bgv(ctx))
+        w += (size_t)cnum * ctx->N * 2 * bgv_prod_limbs(ctx->prm.logN + ctx->prm.logQ) + 64;
       break;
     case FHE_OP_DECRYPT:
       if (logQ > ctx->prm.logQ) return 0;
       w = words_decrypt(ctx, logQ, cnum);
+      if (w && is_bgv(ctx)) w += (size_t)cnum * ctx->N * bgv_prod_limbs(ctx->prm.logN + logQ) + 64;
       break;
     case FHE_OP_KEYGEN: {
       const int r = ctx->R;
@@ -372,8 +474,12 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
   ctx->r_enc = re;
   ctx->r_dec = rd;
   ctx->evk.rows = R;
-  // scratch: inputs, s^2, a s, ring-product workspace
-  const size_t scratch_words = (size_t)N * (2 + 1 + 1 + Lq + Lpq + 1 + Lpq + 2 * Lpq) + 2 * (size_t)R * N;
+  // scratch: inputs, s^2, a s, ring-product workspace (+ BGV reduction scratch)
+  const int nxb = bgv_prod_limbs(ctx->prm.logN + logQ + logP);
+  const size_t bgv_extra = is_bgv(ctx) ? (size_t)N * (4 * (size_t)nxb + 8 + Lq) : 0;
+  const size_t scratch_words =
+      (size_t)N * (2 + 1 + 1 + Lq + Lpq + 1 + (size_t)(nxb > Lpq ? nxb : Lpq) + 2 * Lpq) + 2 * (size_t)R * N +
+      bgv_extra;
   uint32_t* scratch = (uint32_t*)ctx_alloc(ctx, scratch_words * 4);
   if (!scratch) {
     set_error("keygen: scratch allocation failed");
@@ -384,9 +490,10 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
   uint32_t* d_apk = (uint32_t*)(d_eev + N);
   uint32_t* d_aev = d_apk + (size_t)Lq * N;
   uint32_t* d_s2 = d_aev + (size_t)Lpq * N;        // 1 limb two's complement
-  uint32_t* d_t = d_s2 + N;                        // Lpq limbs two's complement of a_ev s
-  uint32_t* d_evl = d_t + (size_t)Lpq * N;         // [2][Lpq][N] evk limbs
+  uint32_t* d_t = d_s2 + N;                        // two's complement of a_ev s (Lpq, BGV nxb limbs)
+  uint32_t* d_evl = d_t + (size_t)(nxb > Lpq ? nxb : Lpq) * N;  // [2][Lpq][N] evk limbs
   uint32_t* rws = d_evl + 2 * (size_t)Lpq * N;     // 2 R N
+  uint32_t* bsc = rws + 2 * (size_t)R * N;         // BGV: reduction scratch, then canonical a_pk
   cudaStream_t st = 0;
   int rc = FHE_OK;
   auto fail = [&](int code) {
@@ -401,6 +508,46 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
     set_error("keygen: upload failed");
     return fail(FHE_ECUDA);
   }
+  if (is_bgv(ctx)) {
+    // BGV: pk = (-a s + t e, a) mod Q_L; evk = (-a' s + t e' + P s^2, a') mod P Q_L; inputs reduced first
+    const int L = ctx->prm.bgv_levels;
+    uint32_t* d_apk_c = bsc + (size_t)N * (4 * (size_t)nxb + 8);
+    if ((rc = launch_bgv_reduce(ctx, d_apk, Lq, 0, 0, 1, 1, false, false, nullptr, nullptr, 0, nullptr, 0, 0, 0,
+                                d_apk_c, 0, 0, L, st)))
+      return fail(rc);
+    const int nx1 = bgv_prod_limbs(ctx->prm.logN + logQ);
+    EpiArgs ek;
+    ek.kind = Epi::kStore;
+    ek.out_bits = 32 * nx1;
+    ek.out_limbs = nx1;
+    if ((rc = ring_product(ctx, d_apk_c, Lq, nullptr, nullptr, 0, ctx->d_s, re, d_t, ek, rws, st))) return fail(rc);
+    if ((rc = launch_bgv_reduce(ctx, d_t, nx1, 0, 0, 1, 1, true, true, d_epk, nullptr, 0, nullptr, 0, 0, 0, ctx->d_pk,
+                                0, 0, L, st)))
+      return fail(rc);
+    if (cudaMemcpy(ctx->d_pk + (size_t)Lq * N, d_apk_c, (size_t)Lq * N * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+      return fail(FHE_ECUDA);
+    // a' canonical mod P Q_L into the second evk poly
+    if ((rc = launch_bgv_modpq(ctx, d_aev, Lpq, false, false, nullptr, nullptr, d_evl + (size_t)Lpq * N, Lpq, bsc,
+                               st)))
+      return fail(rc);
+    EpiArgs e1;
+    e1.kind = Epi::kStore;
+    e1.out_bits = 32;
+    e1.out_limbs = 1;
+    if ((rc = ring_product(ctx, nullptr, 0, ctx->d_s, nullptr, 0, ctx->d_s, primes_for_bound(ctx, ctx->prm.logN + 1),
+                           d_s2, e1, rws, st)))
+      return fail(rc);
+    const int nx2 = bgv_prod_limbs(ctx->prm.logN + logQ + logP);
+    EpiArgs e2;
+    e2.kind = Epi::kStore;
+    e2.out_bits = 32 * nx2;
+    e2.out_limbs = nx2;
+    if ((rc = ring_product(ctx, d_evl + (size_t)Lpq * N, Lpq, nullptr, nullptr, 0, ctx->d_s,
+                           primes_for_bound(ctx, ctx->prm.logN + logQ + logP), d_t, e2, rws, st)))
+      return fail(rc);
+    if ((rc = launch_bgv_modpq(ctx, d_t, nx2, true, true, d_eev, (const int32_t*)d_s2, d_evl, Lpq, bsc, st)))
+      return fail(rc);
+  } else {
   // pk = (-a s + e, a) mod Q
   {
     EpiArgs e;
@@ -436,6 +583,7 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
   if (rc) return fail(rc);
   if (cudaMemcpy(d_evl + (size_t)Lpq * N, d_aev, (size_t)Lpq * N * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
     return fail(FHE_ECUDA);
+  }
   // resident NTT forms
   if ((rc = to_ntt_form(ctx, d_evl, Lpq, 2, R, ctx->evk.ntt, st))) return fail(rc);
   if ((rc = to_ntt_form(ctx, ctx->d_pk, Lq, 2, re, ctx->d_pk_ntt, st))) return fail(rc);
@@ -451,6 +599,10 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
 }
 
 int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e) {
+  if (ctx && is_bgv(ctx)) {
+    set_error("keygen_rotation: CKKS only");
+    return FHE_EINVAL;
+  }
   if (!ctx || !a || !e) {
     set_error("keygen_rotation: null argument");
     return FHE_EINVAL;
@@ -536,11 +688,28 @@ int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t
     return FHE_EWORKSPACE;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const int nxe = is_bgv(ctx) ? bgv_prod_limbs(ctx->prm.logN + ctx->prm.logQ) : 0;
+  uint32_t* T = is_bgv(ctx) ? cv.take((size_t)cnum * 2 * nxe * N) : nullptr;
+  if (!cv.ok) {
+    set_error("encrypt: workspace too small");
+    return FHE_EWORKSPACE;
+  }
   RET_IF(launch_lift_small(ctx, v, true, N, Y, 2 * (size_t)re * N, cnum, re, st));
   RET_IF(launch_ntt(ctx, Y, cnum, re, 2 * re, re, false, st));
   SwitchKey pk{ctx->d_pk_ntt, re};
   RET_IF(launch_pointwise_key(ctx, Y, pk.ntt, pk.rows, re, cnum, st));
   RET_IF(launch_ntt(ctx, Y, cnum * 2, re, re, re, true, st));
+  if (is_bgv(ctx)) {  // exact v pk, then (+ m + t e) mod Q_l
+    EpiArgs ex;
+    ex.kind = Epi::kStore;
+    ex.out_bits = 32 * nxe;
+    ex.out_limbs = nxe;
+    RET_IF(launch_garner(ctx, Y, (size_t)re * N, 2 * (size_t)re * N, re, 2, cnum, T, (size_t)nxe * N,
+                         2 * (size_t)nxe * N, ex, st));
+    RET_IF(launch_bgv_reduce(ctx, T, nxe, (size_t)nxe * N, 2 * (size_t)nxe * N, 2, cnum, true, false, e0, e1, N, pt, 1,
+                             0, (size_t)L * N, out->data, (size_t)L * N, 2 * (size_t)L * N, out->level, st));
+    return check_launch();
+  }
   EpiArgs e;
   e.kind = Epi::kAddSmall;
   e.out_bits = logQ;
@@ -575,10 +744,26 @@ int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size
     return FHE_EWORKSPACE;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const int nxd = is_bgv(ctx) ? bgv_prod_limbs(ctx->prm.logN + logQ) : 0;
+  uint32_t* T = is_bgv(ctx) ? cv.take((size_t)cnum * nxd * N) : nullptr;
+  if (!cv.ok) {
+    set_error("decrypt: workspace too small");
+    return FHE_EWORKSPACE;
+  }
   RET_IF(launch_lift(ctx, in->data + (size_t)L * N, L, 0, 2 * (size_t)L * N, Y, 0, (size_t)rd * N, 1, cnum, rd, st));
   RET_IF(launch_ntt(ctx, Y, cnum, rd, rd, rd, false, st));
   RET_IF(launch_pointwise_mul(ctx, Y, Y, (size_t)rd * N, ctx->d_s_ntt, 0, rd, cnum, st));
   RET_IF(launch_ntt(ctx, Y, cnum, rd, rd, rd, true, st));
+  if (is_bgv(ctx)) {  // exact a s, then [[b + a s]_{Q_l}]_t, one word per coefficient
+    EpiArgs ex;
+    ex.kind = Epi::kStore;
+    ex.out_bits = 32 * nxd;
+    ex.out_limbs = nxd;
+    RET_IF(launch_garner(ctx, Y, 0, (size_t)rd * N, rd, 1, cnum, T, 0, (size_t)nxd * N, ex, st));
+    RET_IF(launch_bgv_decrypt(ctx, T, nxd, (size_t)nxd * N, in->data, 2 * (size_t)L * N, pt_out, N, cnum, in->level,
+                              st));
+    return check_launch();
+  }
   EpiArgs e;
   e.kind = Epi::kDecrypt;
   e.out_bits = logQ;
@@ -597,14 +782,18 @@ int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, 
 
 int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,
                            size_t ws_bytes, void* stream) {
-  if (k < 1) {
-    set_error("mult_relin_rescale: k = %d < 1", k);
+  if (k < 1 || (ctx && is_bgv(ctx))) {
+    set_error("mult_relin_rescale: CKKS only, k >= 1 (k = %d)", k);
     return FHE_EINVAL;
   }
   return mult_impl(ctx, a, b, k, out, ws, ws_bytes, stream);
 }
 
 int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream) {
+  if (ctx && is_bgv(ctx)) {
+    set_error("rescale: CKKS only (BGV uses fhe_moddown)");
+    return FHE_EINVAL;
+  }
   if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || k < 1 || out->logQ != in->logQ - k || out->cnum != in->cnum) {
     set_error("rescale: bad arguments");
     return FHE_EINVAL;
@@ -621,6 +810,16 @@ int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
   if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ > in->logQ || out->cnum != in->cnum) {
     set_error("moddown: bad arguments");
     return FHE_EINVAL;
+  }
+  if (is_bgv(ctx)) {  // modulus switch Q_l -> Q_{l-1}
+    if (out->level != in->level - 1 || out->data == in->data) {
+      set_error("moddown (BGV): one level per call (out->level = in->level - 1), no aliasing");
+      return FHE_ELEVEL;
+    }
+    const size_t N = ctx->N;
+    RET_IF(launch_bgv_modswitch(ctx, in->data, (size_t)limbs_for_bits(in->logQ) * N, out->data,
+                                (size_t)limbs_for_bits(out->logQ) * N, in->cnum * 2, in->level, (cudaStream_t)stream));
+    return check_launch();
   }
   if (out->data == in->data && limbs_for_bits(out->logQ) != limbs_for_bits(in->logQ)) {
     set_error("moddown: in-place drop must keep the limb count");
@@ -639,6 +838,15 @@ static int addsub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, i
     set_error("add/sub/negate: operand levels differ");
     return FHE_ELEVEL;
   }
+  if (is_bgv(ctx)) {
+    if ((mode != 2 && b->level != a->level) || out->level != a->level) {
+      set_error("add/sub/negate (BGV): levels differ");
+      return FHE_ELEVEL;
+    }
+    RET_IF(launch_bgv_addsub(ctx, a->data, mode == 2 ? a->data : b->data, out->data, a->cnum * 2, mode, a->level,
+                             (cudaStream_t)stream));
+    return check_launch();
+  }
   RET_IF(launch_addsub(ctx, a->data, mode == 2 ? a->data : b->data, out->data, a->logQ, a->cnum * 2, mode,
                        (cudaStream_t)stream));
   return check_launch();
@@ -653,6 +861,10 @@ int fhe_negate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
   return addsub(ctx, in, nullptr, out, 2, stream);
 }
 int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void* stream) {
+  if (ctx && is_bgv(ctx)) {
+    set_error("mult_const: CKKS only");
+    return FHE_EINVAL;
+  }
   if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
       c == INT32_MIN) {
     set_error("mult_const: bad arguments");
@@ -663,6 +875,10 @@ int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void*
 }
 
 int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
+  if (ctx && is_bgv(ctx)) {
+    set_error("rotate: CKKS only");
+    return FHE_EINVAL;
+  }
   if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
       out->data == in->data) {
     set_error("rotate: bad arguments");

@@ -18,6 +18,8 @@ namespace fhe {
 constexpr int kMaxPrimes = 256;    // NTT primes available to one context
 constexpr int kMaxLimbs = 128;     // widest big integer a ring product emits (4096 bits)
 constexpr int kMaxLiftLimbs = 128; // widest operand a ring product lifts
+constexpr int kLiftDigits = 64;    // 24-bit digits of the digit-lift path (operands up to 48 limbs)
+constexpr int kCrtDigits = 176;    // 24-bit digit columns of the direct CRT (22 blocks of 8)
 constexpr int kMaxLogN = 16;
 
 // Error reporting (thread-local message, see fhe_last_error).
@@ -39,6 +41,9 @@ struct SwitchKey {
   uint32_t* ntt = nullptr;
   int rows = 0;
 };
+
+struct BgvLevel;
+struct BgvConsts;
 
 // Per-kernel-class launch counters and optional CUDA-event timing.
 struct Profile {
@@ -88,6 +93,7 @@ struct fhe_ctx {
   uint32_t* d_nscale = nullptr;   // [R]  N^-1 * 2^32 mod q (INTT scale, undoes one Montgomery factor)
   uint32_t* d_nscale_sh = nullptr;// [R]
   uint32_t* d_pow2 = nullptr;     // [R][kMaxLiftLimbs] 2^(32 l) mod q
+  uint32_t* d_pow24 = nullptr;    // [R][kLiftDigits] 2^(24 m) mod q
   uint32_t* d_red = nullptr;      // [R][4] {2^32 mod q, shoup, 2^64 mod q, shoup}
   uint2* d_garner = nullptr;      // [R][R] at [k*R + j] = {[q_j^-1]_{q_k}, shoup}, j < k
   uint32_t* d_mprod = nullptr;    // [R+1][kMaxLimbs] prod_{i<k} q_i mod 2^(32 kMaxLimbs)
@@ -96,7 +102,12 @@ struct fhe_ctx {
   uint2* d_crt_inv = nullptr;     // [R(R+1)/2] {[(M_r / q_i)^-1]_{q_i}, shoup}
   uint32_t* d_crt_negm = nullptr; // [R+1][kMaxLimbs] (-M_r) mod 2^(32 kMaxLimbs)
   float* d_invq = nullptr;        // [R] 1/q_i rounded to fp32
+  uint32_t* d_crt_dig = nullptr;  // per r: [r+1][kCrtDigits] 24-bit digits of (M_r/q_i) mod 2^4096, last row -M_r
   int crt_mode = 0;               // 0 direct CRT, 1 Garner (Eq. garner_mrc)
+  // BGV (scheme FHE_SCHEME_BGV): chain constants per level, and bit lengths of Q_l
+  fhe::BgvLevel* d_bgv_levels = nullptr;
+  fhe::BgvConsts* d_bgv_consts = nullptr;
+  std::vector<int> bgv_bits;
 
   // keys (resident)
   bool have_keys = false;

@@ -230,94 +230,94 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
 // dense part sum_i y_i (M/q_i) is a [coefficients x r] by [r x LB-limbs]
 // product: one 32x32->64 multiply-add per (prime, limb), with the constant
 // rows staged in shared memory and read as 128-bit broadcasts.
+// Column form of the dense product: the constants are held as 24-bit digits,
+// so each product y_i d (y_i < 2^31, d < 2^24) is below 2^55 and a whole
+// column sum over r + 1 <= 257 terms fits one 64-bit register -- one
+// 32x32->64 multiply-add per (prime, digit), no carry chain.  The y_i sit in
+// the thread's shared-memory column; columns are taken 8 at a time (192 bits
+// = 6 limbs), normalised into limbs kept in registers, the block's carry
+// passed on.  kappa enters as one more term with the digits of -M.
 template <int LB>
-__global__ void __launch_bounds__(kCrtThreads, (LB <= 64 ? 4 : (LB <= 96 ? 3 : 2))) k_crt_direct(const uint32_t* __restrict__ in, size_t in_pstride,
+__global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* __restrict__ in, size_t in_pstride,
                                                                size_t in_bstride, int r, int npoly,
                                                                uint32_t* __restrict__ out, size_t out_pstride,
                                                                size_t out_bstride, EpiArgs epi, int N,
                                                                const uint32_t* __restrict__ qtab,
                                                                const uint2* __restrict__ cinv,
-                                                               const uint32_t* __restrict__ qhat,
-                                                               const uint32_t* __restrict__ negm,
+                                                               const uint32_t* __restrict__ dig,
                                                                const float* __restrict__ invq) {
-  // The LB limbs are split into NSEG segments with their own carry chains and
-  // 64-bit carry-out counters: the chains are independent within a prime, so
-  // the multiply-adds of different segments overlap; the counters are folded
-  // in once at the end.
-  constexpr int NSEG = (LB % 16 == 0 && LB >= 32) ? 4 : (LB % 8 == 0 && LB >= 16 ? 2 : 1);
-  constexpr int SEG = LB / NSEG;
-  static_assert(SEG % 4 == 0, "segments are read as 128-bit constant vectors");
-  extern __shared__ uint32_t sv[];  // first the [r][LB] constant rows, then the [LB+2][T] limb columns
+  constexpr int NBLK = (LB + 5) / 6;  // 6-limb blocks of 8 digit columns
+  static_assert(8 * NBLK <= kCrtDigits, "digit table too short");
+  extern __shared__ uint32_t sv[];  // [rows][kCrtThreads] y_0..y_{r-1}, kappa (later the limb column),
+                                    // then [2][r+1][8] digit columns of the current block
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < r * LB; idx += blockDim.x) sv[idx] = __ldg(qhat + (size_t)(idx / LB) * kMaxLimbs + idx % LB);
-  __syncthreads();
+  const int rows = (r + 1) > (LB + 2) ? (r + 1) : (LB + 2);
+  uint32_t* cbase = sv + (size_t)rows * kCrtThreads;
   const int n = blockIdx.x * blockDim.x + tid;
   const bool active = n < N;
   const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
-  uint32_t acc[LB];
-#pragma unroll
-  for (int l = 0; l < LB; ++l) acc[l] = 0;
+  // 1. y_i = [x_i (M/q_i)^-1]_{q_i} and the fp32 quotient estimate
   if (active) {
     const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
-    uint64_t cout[NSEG];
-#pragma unroll
-    for (int g = 0; g < NSEG; ++g) cout[g] = 0;
     float fs = 0.f;
-    uint32_t x_next = __ldg(src);
-    uint32_t x_next2 = r > 1 ? __ldg(src + N) : 0u;
+    uint32_t xn = __ldg(src);
     for (int i = 0; i < r; ++i) {
-      const uint32_t x = x_next;
-      x_next = x_next2;
-      if (i + 2 < r) x_next2 = __ldg(src + (size_t)(i + 2) * N);  // two primes ahead
+      const uint32_t x = xn;
+      if (i + 1 < r) xn = __ldg(src + (size_t)(i + 1) * N);
       const uint2 ci = __ldg(cinv + i);
       const uint32_t y = shoup_mul(x, ci.x, ci.y, __ldg(qtab + i));
       fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
-      const uint4* Q = reinterpret_cast<const uint4*>(sv + i * LB);
-      uint32_t c[NSEG];
-#pragma unroll
-      for (int g = 0; g < NSEG; ++g) c[g] = 0;
-#pragma unroll
-      for (int l4 = 0; l4 < SEG / 4; ++l4) {
-#pragma unroll
-        for (int g = 0; g < NSEG; ++g) {
-          const int l = g * SEG + 4 * l4;
-          const uint4 qv = Q[l / 4];
-          uint64_t t;
-          t = (uint64_t)y * qv.x + acc[l + 0]; t += c[g]; acc[l + 0] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
-          t = (uint64_t)y * qv.y + acc[l + 1]; t += c[g]; acc[l + 1] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
-          t = (uint64_t)y * qv.z + acc[l + 2]; t += c[g]; acc[l + 2] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
-          t = (uint64_t)y * qv.w + acc[l + 3]; t += c[g]; acc[l + 3] = (uint32_t)t; c[g] = (uint32_t)(t >> 32);
-        }
-      }
-#pragma unroll
-      for (int g = 0; g < NSEG; ++g) cout[g] += c[g];
+      COL(i) = y;
     }
-    // fold the segment carries: cout[g] belongs at limb (g + 1) SEG (the last one leaves 2^(32 LB))
-#pragma unroll
-    for (int g = 0; g + 1 < NSEG; ++g) {
-      uint64_t cc = cout[g];
-#pragma unroll
-      for (int l = (g + 1) * SEG; l < LB; ++l) {
-        const uint64_t t = (uint64_t)acc[l] + (uint32_t)cc;
-        acc[l] = (uint32_t)t;
-        cc = (cc >> 32) + (t >> 32);
-      }
-    }
-    // X = acc - kappa M = acc + kappa (-M)  (mod 2^(32 LB))
-    const uint32_t kappa = (uint32_t)__float2int_rn(fs);
-    uint32_t cc = 0;
-#pragma unroll
-    for (int l = 0; l < LB; ++l) {
-      uint64_t t = (uint64_t)kappa * __ldg(negm + l) + acc[l];
-      t += cc;
-      acc[l] = (uint32_t)t;
-      cc = (uint32_t)(t >> 32);
-    }
+    COL(r) = (uint32_t)__float2int_rn(fs);  // kappa, multiplies the -M row
   }
-  __syncthreads();  // the constant rows are dead: the area becomes the limb columns
-  if (!active) return;
+  // 2. column sums, 8 digit columns per block; each block's constants staged in shared memory
+  uint32_t X[6 * NBLK];
+  uint64_t carry = 0;
+  const int terms = r + 1;
 #pragma unroll
-  for (int l = 0; l < LB; ++l) COL(l) = acc[l];
+  for (int blk = 0; blk < NBLK; ++blk) {
+    uint32_t* cb = cbase + (size_t)(blk & 1) * terms * 8;
+    for (int idx = tid; idx < terms * 8; idx += blockDim.x)
+      cb[idx] = __ldg(dig + (size_t)(idx >> 3) * kCrtDigits + 8 * blk + (idx & 7));
+    __syncthreads();
+    uint64_t s0 = carry, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0;
+#pragma unroll 4
+    for (int i = 0; i < terms; ++i) {
+      const uint32_t y = COL(i);
+      const uint4 d0 = *reinterpret_cast<const uint4*>(cb + 8 * i);
+      const uint4 d1 = *reinterpret_cast<const uint4*>(cb + 8 * i + 4);
+      s0 += (uint64_t)y * d0.x;
+      s1 += (uint64_t)y * d0.y;
+      s2 += (uint64_t)y * d0.z;
+      s3 += (uint64_t)y * d0.w;
+      s4 += (uint64_t)y * d1.x;
+      s5 += (uint64_t)y * d1.y;
+      s6 += (uint64_t)y * d1.z;
+      s7 += (uint64_t)y * d1.w;
+    }
+    // normalise 8 digit columns into 6 limbs; the rest carries into the next block
+    uint32_t dd[8];
+    s1 += s0 >> 24; dd[0] = (uint32_t)s0 & 0xFFFFFFu;
+    s2 += s1 >> 24; dd[1] = (uint32_t)s1 & 0xFFFFFFu;
+    s3 += s2 >> 24; dd[2] = (uint32_t)s2 & 0xFFFFFFu;
+    s4 += s3 >> 24; dd[3] = (uint32_t)s3 & 0xFFFFFFu;
+    s5 += s4 >> 24; dd[4] = (uint32_t)s4 & 0xFFFFFFu;
+    s6 += s5 >> 24; dd[5] = (uint32_t)s5 & 0xFFFFFFu;
+    s7 += s6 >> 24; dd[6] = (uint32_t)s6 & 0xFFFFFFu;
+    dd[7] = (uint32_t)s7 & 0xFFFFFFu;
+    carry = s7 >> 24;
+    X[6 * blk + 0] = dd[0] | (dd[1] << 24);
+    X[6 * blk + 1] = (dd[1] >> 8) | (dd[2] << 16);
+    X[6 * blk + 2] = (dd[2] >> 16) | (dd[3] << 8);
+    X[6 * blk + 3] = dd[4] | (dd[5] << 24);
+    X[6 * blk + 4] = (dd[5] >> 8) | (dd[6] << 16);
+    X[6 * blk + 5] = (dd[6] >> 16) | (dd[7] << 8);
+  }
+  if (!active) return;
+  // 3. epilogue on the limb column (the y rows are dead)
+#pragma unroll
+  for (int l = 0; l < LB; ++l) COL(l) = X[l];
   crt_epilogue(sv, tid, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
 }
 
@@ -326,16 +326,17 @@ static int direct_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size
                          uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, cudaStream_t st) {
   const int N = ctx->N;
   const int threads = kCrtThreads;
-  const size_t rows_words = (size_t)r * LB, col_words = (size_t)(LB + 2) * threads;
-  const size_t smem = 4 * (rows_words > col_words ? rows_words : col_words);
+  const int rows = (r + 1) > (LB + 2) ? (r + 1) : (LB + 2);
+  const size_t smem = (size_t)rows * threads * 4 + 2 * (size_t)(r + 1) * 8 * 4;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_crt_direct<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((N + threads - 1) / threads, npoly * nbatch);
   ProfScope ps(ctx, FHE_K_CRT, 1, st);
   const size_t off = (size_t)r * (r - 1) / 2;
+  const size_t dbase = (size_t)(r - 1) * (r + 2) / 2;
   k_crt_direct<LB><<<grid, threads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q,
-                                                 ctx->d_crt_inv + off, ctx->d_crt_qhat + off * kMaxLimbs,
-                                                 ctx->d_crt_negm + (size_t)r * kMaxLimbs, ctx->d_invq);
+                                                 ctx->d_crt_inv + off, ctx->d_crt_dig + dbase * kCrtDigits,
+                                                 ctx->d_invq);
   return FHE_OK;
 }
 

@@ -71,6 +71,63 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
   }
 }
 
+
+// Digit lift for operands of up to 48 limbs: the coefficient is re-read as
+// 24-bit digits z_m (A = sum_m z_m 2^(24 m)), so every product z_m (2^(24 m)
+// mod q_i) is below 2^55 and up to 256 of them add up in one 64-bit register
+// without any overflow handling: one 32x32->64 multiply-add per digit.
+template <int LB>
+__global__ void __launch_bounds__(kLiftThreads) k_lift_digits(const uint32_t* __restrict__ src, int L,
+                                                              size_t src_pstride, size_t src_bstride,
+                                                              uint32_t* __restrict__ dst, size_t dst_pstride,
+                                                              size_t dst_bstride, int npoly, int r, int N,
+                                                              const uint32_t* __restrict__ pow24,
+                                                              const uint32_t* __restrict__ qtab,
+                                                              const uint32_t* __restrict__ red) {
+  constexpr int MD = (32 * LB + 23) / 24;  // digits covering LB limbs
+  constexpr int MP = (MD + 3) & ~3;        // padded to 128-bit loads
+  static_assert(MP <= kLiftDigits, "digit table too short");
+  extern __shared__ uint32_t sc[];  // [r][MP]
+  for (int idx = threadIdx.x; idx < r * MP; idx += blockDim.x) {
+    const int i = idx / MP, m = idx % MP;
+    sc[idx] = m < MD ? pow24[(size_t)i * kLiftDigits + m] : 0u;
+  }
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
+  const uint32_t* s = src + (size_t)b * src_bstride + (size_t)poly * src_pstride + n;
+  uint32_t x[LB + 1];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) x[l] = (l < L) ? __ldg(s + (size_t)l * N) : 0u;
+  x[LB] = 0;
+  uint32_t z[MP];
+#pragma unroll
+  for (int m = 0; m < MP; ++m) {
+    const int o = 24 * m, l = o >> 5, sh = o & 31;
+    z[m] = (m < MD && l < LB) ? (__funnelshift_r(x[l], x[l + 1], sh) & 0xFFFFFFu) : 0u;
+  }
+  uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n;
+  const int md_live = (32 * L + 23) / 24;  // digits of the live limbs
+  for (int i = 0; i < r; ++i) {
+    const uint4* c4 = reinterpret_cast<const uint4*>(sc + i * MP);
+    uint64_t acc = 0;
+#pragma unroll
+    for (int m4 = 0; m4 < MP / 4; ++m4) {
+      if (4 * m4 < md_live) {
+        const uint4 c = c4[m4];
+        acc += (uint64_t)z[4 * m4] * c.x;
+        acc += (uint64_t)z[4 * m4 + 1] * c.y;
+        acc += (uint64_t)z[4 * m4 + 2] * c.z;
+        acc += (uint64_t)z[4 * m4 + 3] * c.w;
+      }
+    }
+    const uint32_t q = __ldg(qtab + i);
+    d[(size_t)i * N] = reduce96((uint32_t)acc, (uint32_t)(acc >> 32), 0u, q, __ldg(red + 4 * i),
+                                __ldg(red + 4 * i + 1), __ldg(red + 4 * i + 2));
+  }
+}
+
 // Small signed coefficients (secret, ephemeral, error polynomials).
 template <typename T>
 __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint32_t* __restrict__ dst,
@@ -94,6 +151,15 @@ static void lift_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t s
   const int N = ctx->N;
   const int threads = N < kLiftThreads ? N : kLiftThreads;
   dim3 grid((N + threads - 1) / threads, npoly * nbatch);
+  if constexpr (LB <= 48) {
+    constexpr int MP = (((32 * LB + 23) / 24) + 3) & ~3;
+    const size_t smem = (size_t)r * MP * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_lift_digits<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_lift_digits<LB><<<grid, threads, smem, st>>>(src, L, sp, sb, dst, dp, db, npoly, r, N, ctx->d_pow24, ctx->d_q,
+                                                    ctx->d_red);
+    return;
+  }
   size_t smem = (size_t)r * ((L + 3) & ~3) * sizeof(uint32_t);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_lift<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_lift<LB><<<grid, threads, smem, st>>>(src, L, sp, sb, dst, dp, db, npoly, r, N, ctx->d_pow2, ctx->d_q,

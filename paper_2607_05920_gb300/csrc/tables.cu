@@ -195,7 +195,7 @@ int build_tables(fhe_ctx* ctx) {
 
   std::vector<uint32_t> qinv(R), nscale(R), nscale_sh(R), red(4 * (size_t)R);
   std::vector<uint32_t> psi((size_t)R * N), psi_sh((size_t)R * N), ipsi((size_t)R * N), ipsi_sh((size_t)R * N);
-  std::vector<uint32_t> pow2((size_t)R * kMaxLiftLimbs);
+  std::vector<uint32_t> pow2((size_t)R * kMaxLiftLimbs), pow24((size_t)R * kLiftDigits);
   std::vector<uint2> garner((size_t)R * R, make_uint2(0, 0));
   std::vector<uint32_t> mprod((size_t)(R + 1) * kMaxLimbs, 0);
 
@@ -228,6 +228,7 @@ int build_tables(fhe_ctx* ctx) {
     nscale[i] = (uint32_t)mulmod64(ninv, ((uint64_t)1 << 32) % qi, qi);
     nscale_sh[i] = shoup_of(nscale[i], qi);
     for (int l = 0; l < kMaxLiftLimbs; ++l) pow2[(size_t)i * kMaxLiftLimbs + l] = (uint32_t)powmod64(2, 32ull * l, qi);
+    for (int m = 0; m < kLiftDigits; ++m) pow24[(size_t)i * kLiftDigits + m] = (uint32_t)powmod64(2, 24ull * m, qi);
     uint32_t r32 = (uint32_t)(((uint64_t)1 << 32) % qi);
     uint32_t r64 = (uint32_t)mulmod64(r32, r32, qi);
     red[4 * i + 0] = r32;
@@ -302,13 +303,32 @@ int build_tables(fhe_ctx* ctx) {
     for (int i = 0; i < R; ++i) invq[i] = (float)(1.0 / (double)q[i]);
   }
 
+  // the same constants as 24-bit digit columns: set r occupies rows [r(r+1)/2 - 1 ...] -> offset
+  // sum_{r'<r} (r'+1) = r(r+1)/2 - 1 rows... kept simple: rows of set r start at (r-1)(r+2)/2
+  std::vector<uint32_t> dig((size_t)((R) * (R + 3) / 2 + 2) * kCrtDigits, 0);
+  auto digits_of = [](const uint32_t* limbs, uint32_t* out) {
+    for (int m = 0; m < kCrtDigits; ++m) {
+      const int o = 24 * m, l = o >> 5, sh = o & 31;
+      uint64_t w = 0;
+      if (l < kMaxLimbs) w = limbs[l];
+      if (l + 1 < kMaxLimbs) w |= (uint64_t)limbs[l + 1] << 32;
+      out[m] = (uint32_t)(w >> sh) & 0xFFFFFFu;
+    }
+  };
+  for (int r = 1; r <= R; ++r) {
+    const size_t base = (size_t)(r - 1) * (r + 2) / 2;  // sum_{r'=1}^{r-1} (r'+1)
+    const size_t off = (size_t)r * (r - 1) / 2;
+    for (int i = 0; i < r; ++i) digits_of(&qhat[(off + i) * kMaxLimbs], &dig[(base + i) * kCrtDigits]);
+    digits_of(&negm[(size_t)r * kMaxLimbs], &dig[(base + r) * kCrtDigits]);
+  }
+  if (!(ctx->d_crt_dig = upload(ctx, dig))) return FHE_ENOMEM;
   if (!(ctx->d_crt_qhat = upload(ctx, qhat)) || !(ctx->d_crt_inv = upload(ctx, crt_inv)) ||
       !(ctx->d_crt_negm = upload(ctx, negm)) || !(ctx->d_invq = upload(ctx, invq)))
     return FHE_ENOMEM;
   if (!(ctx->d_q = upload(ctx, q)) || !(ctx->d_qinv = upload(ctx, qinv)) || !(ctx->d_psi = upload(ctx, psi)) ||
       !(ctx->d_psi_sh = upload(ctx, psi_sh)) || !(ctx->d_ipsi = upload(ctx, ipsi)) ||
       !(ctx->d_ipsi_sh = upload(ctx, ipsi_sh)) || !(ctx->d_nscale = upload(ctx, nscale)) ||
-      !(ctx->d_nscale_sh = upload(ctx, nscale_sh)) || !(ctx->d_pow2 = upload(ctx, pow2)) ||
+      !(ctx->d_nscale_sh = upload(ctx, nscale_sh)) || !(ctx->d_pow2 = upload(ctx, pow2)) || !(ctx->d_pow24 = upload(ctx, pow24)) ||
       !(ctx->d_red = upload(ctx, red)) || !(ctx->d_garner = upload(ctx, garner)) ||
       !(ctx->d_mprod = upload(ctx, mprod)))
     return FHE_ENOMEM;

@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-iters", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--workload", default="ns", choices=["ns", "batched"],
+                    help="ns: the headline N=2^16 logQ=1200 batch; batched: 512 uneven pairs, graph vs per-op")
     ap.add_argument("--crt", default="direct", choices=["direct", "garner"],
                     help="RNS->limb reconstruction: exact CRT with rounded quotient, or Garner mixed radix")
     return ap.parse_args()
@@ -387,10 +389,83 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """512 CKKS pairs, N in {2^13..2^16}, logQ uniform in [200, 1200], keys per N with logP = 1200:
+    one CUDA-graph launch of the autotuned plan vs per-op launches, identical results."""
+    import numpy as np
+    import torch
+
+    import fhe_synth as fs
+    import paper_2607_05920_gb300 as fhe
+    from paper_2607_05920_gb300 import batch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g = fs.rng(4040)
+    ctxs = {}
+    for logN in (13, 14, 15, 16):
+        N = 1 << logN
+        c = fhe.Context(logN, 1200, 1200)
+        c.keygen(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, 1200), fs.gaussian(g, (), N),
+                 fs.uniform_limbs(g, (), N, 2400), fs.gaussian(g, (), N))
+        ctxs[logN] = c
+    items = []
+    for _ in range(args.cnum if args.cnum != 64 else 512):
+        logN = int(g.choice([13, 14, 15, 16]))
+        logQ = int(g.integers(200, 1201))
+        N = 1 << logN
+        mk = lambda: fhe.Ciphertext(torch.from_numpy(
+            fs.uniform_limbs(g, (1, 2), N, logQ).view(np.int32).copy()).cuda(), logQ)
+        items.append(batch.Item(logN, logQ, mk(), mk()))
+    runner = batch.BatchRunner(ctxs, K_RESCALE)
+    tuned = batch.Autotuner().tune(runner, items, reps=1)
+    plan = runner.plan(items, tuned["schedule"])
+    runner.pack(plan, items)
+    runner.capture(plan)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        runner.graph.replay()
+        runner.per_op(items)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        runner.graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / args.steps
+    e0.record(stream)
+    for _ in range(args.steps):
+        ref = runner.per_op(items)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_op = e0.elapsed_time(e1) / args.steps
+    got = runner.outputs(plan, items)
+    identical = all(torch.equal(got[i], ref[i].data[0]) for i in range(len(items)))
+    launches_graph = sum(16 for _ in plan.groups)
+    line = {
+        "metric": "uneven-batch HMult+relin+rescale pairs/s (N 2^13..2^16, logQ 200..1200)",
+        "value": len(items) / (ms_graph / 1e3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "dtype": "u32",
+        "data": "synthetic (uniform ciphertexts, seeded)",
+        "config": {"workload": "512 CKKS pairs, N uniform in {2^13..2^16}, logQ uniform in [200,1200], logP 1200, "
+                               "scale 2^40, one CUDA-graph launch", "items": len(items),
+                   "schedule": {str(k): v for k, v in tuned["schedule"].items()}, "groups": len(plan.groups)},
+        "per_op": {"value": len(items) / (ms_per_op / 1e3), "ms_per_step": ms_per_op, "launches": 15 * len(items)},
+        "speedup_vs_per_op": ms_per_op / ms_graph, "identical_results": bool(identical),
+        "graph_kernels_approx": launches_graph,
+        "autotune_ms": {str(k): v for k, v in tuned["timings_ms"].items()},
+    }
+    print(json.dumps(line), flush=True)
+    for c in ctxs.values():
+        c.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -67,6 +67,7 @@ extern "C" {
 #define FHE_OP_DECRYPT 4   /* fhe_decrypt                              */
 #define FHE_OP_KEYGEN 5    /* fhe_keygen, fhe_keygen_rotation (cnum 1) */
 #define FHE_OP_RING_MUL 6  /* fhe_ring_mul with logQ = max operand bits */
+#define FHE_OP_MULT_RAGGED 7 /* fhe_mult_relin_rescale_ragged, logQ = the largest level */
 
 typedef struct fhe_ctx fhe_ctx;
 
@@ -181,6 +182,19 @@ int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, 
  * the relinearisation epilogue; out->logQ must equal a->logQ - k. */
 int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,
                            size_t ws_bytes, void* stream);
+
+/* Batched multiply + relinearise + rescale over ciphertext pairs at
+ * DIFFERENT levels of one ring (the CipherTensor batch of Sec. 6 with a
+ * per-ciphertext modulus; CKKS only).  Item i has modulus 2^item_logQ[i]
+ * (device int32_t[cnum], each <= logQ_max); a, b, out are device
+ * uint32_t[cnum][2][L_pad][N] with L_pad >= ceil(logQ_max/32): item i's limbs
+ * at and above bit item_logQ[i] must be zero on input and are zero on output.
+ * Result i = fhe_mult_relin_rescale of pair i at its own level (modulus
+ * 2^(item_logQ[i] - k)).  Prime counts and key rows are those of logQ_max,
+ * which is exact for every item.  Workspace: FHE_OP_MULT_RAGGED at logQ_max. */
+int fhe_mult_relin_rescale_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int cnum,
+                                  int L_pad, const int32_t* item_logQ, int logQ_max, int k, void* ws,
+                                  size_t ws_bytes, void* stream);
 
 /* Rescale (rescaleBy_pairwise_into, Sec. 6): out = round(in / 2^k) mod
  * 2^(logQ - k), halves rounded up; out->logQ must equal in->logQ - k. */

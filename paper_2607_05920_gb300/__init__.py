@@ -43,6 +43,7 @@ FHE_OP_ENCRYPT = 3
 FHE_OP_DECRYPT = 4
 FHE_OP_KEYGEN = 5
 FHE_OP_RING_MUL = 6
+FHE_OP_MULT_RAGGED = 7
 
 
 class FheParams(ctypes.Structure):
@@ -79,6 +80,7 @@ SIGNATURES = {
     "fhe_mult_relin_rescale": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P,
                                     _SZ, _P]),
     "fhe_rescale": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P]),
+    "fhe_mult_relin_rescale_ragged": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _I, _P, _SZ, _P]),
     "fhe_moddown": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_rotate": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P, _SZ, _P]),
     "fhe_add": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
@@ -376,6 +378,19 @@ def fhe_mult_relin_rescale_noalloc(ctx: Context, a: Ciphertext, b: Ciphertext, k
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_mult_relin_rescale_noalloc(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k),
                                               ctypes.byref(co), _stream()), "fhe_mult_relin_rescale_noalloc")
+
+
+def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: int, k: int) -> None:
+    """Pairs at different levels in one batch: a, b, out (cnum, 2, L_pad, N) int32 CUDA tensors,
+    item_logQ a CUDA int32 tensor (cnum,)."""
+    import torch
+
+    cnum, two, L_pad, N = a.shape
+    ws = ctx.workspace(FHE_OP_MULT_RAGGED, logQ_max, cnum)
+    _check(lib.fhe_mult_relin_rescale_ragged(
+        ctx.handle, _dev(a, torch.int32, (cnum, 2, L_pad, N)), _dev(b, torch.int32, (cnum, 2, L_pad, N)),
+        _dev(out, torch.int32, (cnum, 2, L_pad, N)), int(cnum), int(L_pad), _dev(item_logQ, torch.int32, (cnum,)),
+        int(logQ_max), int(k), ws.data_ptr(), ws.numel(), _stream()), "fhe_mult_relin_rescale_ragged")
 
 
 def fhe_rescale(ctx: Context, ct: Ciphertext, k: int, out: Ciphertext) -> None:

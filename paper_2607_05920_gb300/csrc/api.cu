@@ -158,7 +158,7 @@ uint32_t galois_of_step(int N, int step) {
 // key K = [2][krows][N]; result (add + round(Y / P)) mod 2^logQ into out.
 int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int nbatch, int logQ, int k2,
                     const uint32_t* add, size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out,
-                    cudaStream_t st) {
+                    cudaStream_t st, const int32_t* item_bits = nullptr, int out_limbs_pad = 0) {
   const size_t N = ctx->N;
   RET_IF(launch_ntt(ctx, Y, nbatch, rk, 2 * rk, rk, false, st));
   RET_IF(launch_pointwise_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
@@ -174,6 +174,8 @@ int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int n
   epi.add_pstride = add_pstride;
   epi.add_bstride = add_bstride;
   epi.add_polys = add_polys;
+  epi.item_bits = item_bits;
+  if (out_limbs_pad > 0) epi.out_limbs = out_limbs_pad;
   const size_t Lo = epi.out_limbs;
   RET_IF(launch_garner(ctx, Y, (size_t)rk * N, 2 * (size_t)rk * N, rk, 2, nbatch, out, Lo * N, 2 * Lo * N, epi, st));
   return check_launch();
@@ -230,6 +232,41 @@ int mult_bgv(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* 
                               3 * (size_t)L * N, out->data, (size_t)L * N, 2 * (size_t)L * N, cnum, level, Z,
                               (size_t)nz * N, 2 * (size_t)nz * N, st));
   return check_launch();
+}
+
+// Ragged batch: item i at modulus 2^item_bits[i] (device array), all stored in
+// L_pad limbs; prime counts and key rows from the largest level (exact for all).
+int mult_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int cnum, int L_pad,
+                const int32_t* item_bits, int logQ_max, int k2, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int L = L_pad;
+  const int rt = r_tensor(ctx, logQ_max), rk = r_keyswitch(ctx, logQ_max);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* X = cv.take((size_t)cnum * 4 * rt * N);
+  uint32_t* D = cv.take((size_t)cnum * 3 * L * N);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("mult_ragged: workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  const size_t ctw = 2 * (size_t)L * N;
+  RET_IF(launch_lift(ctx, a, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
+  RET_IF(launch_lift(ctx, b, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N, 4 * (size_t)rt * N, 2,
+                     cnum, rt, st));
+  RET_IF(launch_ntt(ctx, X, cnum * 4, rt, rt, rt, false, st));
+  RET_IF(launch_pointwise_tensor(ctx, X, rt, cnum, st));
+  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  EpiArgs e0;
+  e0.kind = Epi::kStore;
+  e0.out_bits = logQ_max;
+  e0.item_bits = item_bits;
+  e0.out_limbs = L;
+  RET_IF(launch_garner(ctx, X, (size_t)rt * N, 4 * (size_t)rt * N, rt, 3, cnum, D, (size_t)L * N,
+                       3 * (size_t)L * N, e0, st));
+  RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
+                     st));
+  return key_switch_tail(ctx, Y, ctx->evk, rk, cnum, logQ_max, k2, D, (size_t)L * N, 3 * (size_t)L * N, 2, out, st,
+                         item_bits, L);
 }
 
 int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* out, void* ws, size_t ws_bytes,
@@ -433,6 +470,10 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
     }
     case FHE_OP_RING_MUL:
       w = words_ringmul(ctx, logQ, cnum);
+      break;
+    case FHE_OP_MULT_RAGGED:
+      if (logQ > ctx->prm.logQ) return 0;
+      w = words_mult(ctx, logQ, cnum);
       break;
     default:
       return 0;
@@ -778,6 +819,26 @@ int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size
 int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* ws, size_t ws_bytes,
                    void* stream) {
   return mult_impl(ctx, a, b, 0, out, ws, ws_bytes, stream);
+}
+
+int fhe_mult_relin_rescale_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int cnum,
+                                  int L_pad, const int32_t* item_logQ, int logQ_max, int k, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  if (!ctx || !a || !b || !out || !item_logQ || cnum < 1 || cnum > kMaxCnum || logQ_max < 1 ||
+      logQ_max > ctx->prm.logQ || L_pad < limbs_for_bits(logQ_max) || L_pad > kMaxLiftLimbs || k < 0 ||
+      k >= logQ_max || is_bgv(ctx)) {
+    set_error("mult_relin_rescale_ragged: bad arguments");
+    return FHE_EINVAL;
+  }
+  if (!ctx->have_keys) {
+    set_error("mult_relin_rescale_ragged: no relinearisation key");
+    return FHE_ENOKEY;
+  }
+  if (out == a || out == b) {
+    set_error("mult_relin_rescale_ragged: out aliases an input");
+    return FHE_EINVAL;
+  }
+  return mult_ragged(ctx, a, b, out, cnum, L_pad, item_logQ, logQ_max, k, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,

@@ -219,6 +219,7 @@ enum class Epi : int {
 struct EpiArgs {
   Epi kind = Epi::kStore;
   int out_bits = 0;          // modulus 2^out_bits of the result
+  const int32_t* item_bits = nullptr;  // if set: per batch item modulus bits (overrides out_bits)
   int out_limbs = 0;         // limbs written per coefficient
   const uint32_t* add = nullptr;  // limbs [L_add][N] per poly (batch stride add_bstride)
   int add_limbs = 0;

@@ -62,7 +62,7 @@ __device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, in
                                           int b, int n, int N, uint32_t* __restrict__ out, size_t out_pstride,
                                           size_t out_bstride) {
 
-  const int ob = epi.out_bits;
+  const int ob = epi.item_bits ? __ldg(epi.item_bits + b) : epi.out_bits;
   int nl = LB;  // live limbs in the column
   if (epi.kind == Epi::kRelin) {
     if (epi.shift > 0) col_add_pow2(sv, tid, LB, epi.shift - 1);
@@ -260,14 +260,23 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
   if (active) {
     const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n;
     float fs = 0.f;
-    uint32_t xn = __ldg(src);
-    for (int i = 0; i < r; ++i) {
-      const uint32_t x = xn;
-      if (i + 1 < r) xn = __ldg(src + (size_t)(i + 1) * N);
-      const uint2 ci = __ldg(cinv + i);
-      const uint32_t y = shoup_mul(x, ci.x, ci.y, __ldg(qtab + i));
-      fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
-      COL(i) = y;
+    constexpr int PF = 8;  // residue loads kept in flight
+    uint32_t xb[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) xb[k] = k < r ? __ldg(src + (size_t)k * N) : 0u;
+    for (int i0 = 0; i0 < r; i0 += PF) {
+#pragma unroll
+      for (int k = 0; k < PF; ++k) {
+        const int i = i0 + k;
+        if (i < r) {
+          const uint32_t x = xb[k];
+          if (i + PF < r) xb[k] = __ldg(src + (size_t)(i + PF) * N);
+          const uint2 ci = __ldg(cinv + i);
+          const uint32_t y = shoup_mul(x, ci.x, ci.y, __ldg(qtab + i));
+          fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
+          COL(i) = y;
+        }
+      }
     }
     COL(r) = (uint32_t)__float2int_rn(fs);  // kappa, multiplies the -M row
   }

@@ -220,6 +220,11 @@ int fhe_negate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
  * integer-encoded scalar). */
 int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void* stream);
 
+/* Add an integer constant (addconst, Sec. 6): coefficient 0 of b gains
+ * value * 2^shift (mod 2^logQ), i.e. every slot gains value 2^shift / Delta.
+ * CKKS only; 0 <= shift < logQ; out may alias in. */
+int fhe_add_const(fhe_ctx* ctx, const fhe_ct* in, int64_t value, int shift, fhe_ct* out, void* stream);
+
 /* The big-integer negacyclic multiplier of Sec. 5 on its own:
  *   out = a * b mod 2^logOut in Z[X]/(X^N + 1),
  * a: device uint32_t[cnum][La][N], b: device uint32_t[cnum][Lb][N] (unsigned

@@ -88,6 +88,7 @@ SIGNATURES = {
     "fhe_negate": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_mult_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int32, ctypes.POINTER(FheCt), _P]),
     "fhe_ring_mul": (_I, [_P, _P, _I, _P, _I, _I, _P, _I, _P, _SZ, _P]),
+    "fhe_add_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int64, _I, ctypes.POINTER(FheCt), _P]),
     "fhe_primes_for_bound": (_I, [_I]),
     "fhe_mult_relin_rescale_noalloc": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I,
                                             ctypes.POINTER(FheCt), _P]),
@@ -144,6 +145,8 @@ class Ciphertext:
         return int(self.data.shape[0])
 
     def c(self) -> FheCt:
+        if not self.data.is_contiguous():
+            raise ValueError("ciphertext tensor must be contiguous (the C ABI reads a dense [cnum][2][L][N] block)")
         return FheCt(self.data.data_ptr(), self.cnum, self.logQ, self.level)
 
 
@@ -380,13 +383,14 @@ def fhe_mult_relin_rescale_noalloc(ctx: Context, a: Ciphertext, b: Ciphertext, k
                                               ctypes.byref(co), _stream()), "fhe_mult_relin_rescale_noalloc")
 
 
-def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: int, k: int) -> None:
+def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: int, k: int, ws=None) -> None:
     """Pairs at different levels in one batch: a, b, out (cnum, 2, L_pad, N) int32 CUDA tensors,
-    item_logQ a CUDA int32 tensor (cnum,)."""
+    item_logQ a CUDA int32 tensor (cnum,).  `ws`: optional caller workspace (uint8 CUDA tensor)."""
     import torch
 
     cnum, two, L_pad, N = a.shape
-    ws = ctx.workspace(FHE_OP_MULT_RAGGED, logQ_max, cnum)
+    if ws is None:
+        ws = ctx.workspace(FHE_OP_MULT_RAGGED, logQ_max, cnum)
     _check(lib.fhe_mult_relin_rescale_ragged(
         ctx.handle, _dev(a, torch.int32, (cnum, 2, L_pad, N)), _dev(b, torch.int32, (cnum, 2, L_pad, N)),
         _dev(out, torch.int32, (cnum, 2, L_pad, N)), int(cnum), int(L_pad), _dev(item_logQ, torch.int32, (cnum,)),
@@ -403,8 +407,9 @@ def fhe_moddown(ctx: Context, ct: Ciphertext, out: Ciphertext) -> None:
     _check(lib.fhe_moddown(ctx.handle, ctypes.byref(ci), ctypes.byref(co), _stream()), "fhe_moddown")
 
 
-def fhe_rotate(ctx: Context, ct: Ciphertext, step: int, out: Ciphertext) -> None:
-    ws = ctx.workspace(FHE_OP_ROTATE, ct.logQ, ct.cnum)
+def fhe_rotate(ctx: Context, ct: Ciphertext, step: int, out: Ciphertext, ws=None) -> None:
+    if ws is None:
+        ws = ctx.workspace(FHE_OP_ROTATE, ct.logQ, ct.cnum)
     ci, co = ct.c(), out.c()
     _check(lib.fhe_rotate(ctx.handle, ctypes.byref(ci), int(step), ctypes.byref(co), ws.data_ptr(), ws.numel(),
                           _stream()), "fhe_rotate")
@@ -428,6 +433,12 @@ def fhe_negate(ctx: Context, a: Ciphertext, out: Ciphertext) -> None:
 def fhe_mult_const(ctx: Context, a: Ciphertext, c: int, out: Ciphertext) -> None:
     ca, co = a.c(), out.c()
     _check(lib.fhe_mult_const(ctx.handle, ctypes.byref(ca), int(c), ctypes.byref(co), _stream()), "fhe_mult_const")
+
+
+def fhe_add_const(ctx: Context, a: Ciphertext, value: int, shift: int, out: Ciphertext) -> None:
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_add_const(ctx.handle, ctypes.byref(ca), int(value), int(shift), ctypes.byref(co), _stream()),
+           "fhe_add_const")
 
 
 def fhe_ring_mul(ctx: Context, a, b, logOut: int, out) -> None:

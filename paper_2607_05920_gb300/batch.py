@@ -139,7 +139,7 @@ class BatchRunner:
         out = [None] * len(items)
         for g in plan.groups:
             for j, i in enumerate(g.idx):
-                out[i] = g.O[j, :, :limbs(items[i].logQ - self.k)]
+                out[i] = g.O[j, :, :limbs(items[i].logQ - self.k)].contiguous()
         return out
 
     def per_op(self, items: list[Item]) -> list:

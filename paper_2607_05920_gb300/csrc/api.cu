@@ -935,6 +935,19 @@ int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void*
   return check_launch();
 }
 
+int fhe_add_const(fhe_ctx* ctx, const fhe_ct* in, int64_t value, int shift, fhe_ct* out, void* stream) {
+  if (!ctx || is_bgv(ctx) || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
+      shift < 0 || shift >= in->logQ) {
+    set_error("add_const: bad arguments (CKKS, 0 <= shift < logQ)");
+    return FHE_EINVAL;
+  }
+  const size_t bytes = fhe_ct_bytes(ctx->prm.logN, in->logQ, in->cnum);
+  if (out->data != in->data)
+    FHE_CHECK_CUDA(cudaMemcpyAsync(out->data, in->data, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  RET_IF(launch_add_const(ctx, out->data, out->data, value, shift, in->logQ, in->cnum, (cudaStream_t)stream));
+  return check_launch();
+}
+
 int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
   if (ctx && is_bgv(ctx)) {
     set_error("rotate: CKKS only");

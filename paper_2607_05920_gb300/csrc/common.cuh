@@ -248,6 +248,8 @@ int launch_addsub(const fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint
                   int mode /*0 add,1 sub,2 neg(a)*/, cudaStream_t st);
 int launch_mult_const(const fhe_ctx* ctx, const uint32_t* in, int32_t c, uint32_t* out, int logQ, int npolys,
                       cudaStream_t st);
+int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, int shift, int logQ,
+                     int cnum, cudaStream_t st);
 // out[l][n] = sign * in[l][i], kappa_g (X^i -> X^(i g)); polys of L limbs mod 2^logQ.
 int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, uint32_t* out, size_t out_pstride,
                      int L, int logQ, uint32_t g, int npolys, cudaStream_t st);

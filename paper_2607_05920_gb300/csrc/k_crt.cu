@@ -23,7 +23,7 @@ namespace fhe {
 
 constexpr int kCrtThreads = 128;
 
-#define COL(l) sv[(size_t)(l) * kCrtThreads + tid]
+#define COL(l) sv[(size_t)(l) * cstride + tid]
 
 // out_bits-bit mask for limb l
 __device__ __forceinline__ uint32_t limb_mask(int l, int bits) {
@@ -34,7 +34,7 @@ __device__ __forceinline__ uint32_t limb_mask(int l, int bits) {
 }
 
 // column += 2^pos (mod 2^(32 nl))
-__device__ __forceinline__ void col_add_pow2(uint32_t* sv, int tid, int nl, int pos) {
+__device__ __forceinline__ void col_add_pow2(uint32_t* sv, int tid, int cstride, int nl, int pos) {
   int l = pos >> 5;
   uint32_t add = 1u << (pos & 31);
   for (; l < nl && add; ++l) {
@@ -45,7 +45,7 @@ __device__ __forceinline__ void col_add_pow2(uint32_t* sv, int tid, int nl, int 
 }
 
 // column[l] <- (column >> sh)[l] for l < nl_out, reading limbs < nl_in (zero above)
-__device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int nl_in, int nl_out, int sh) {
+__device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int cstride, int nl_in, int nl_out, int sh) {
   const int sl = sh >> 5, sb = sh & 31;
   for (int l = 0; l < nl_out; ++l) {
     const int a = l + sl;
@@ -58,16 +58,16 @@ __device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int nl_in
 // Epilogue on the thread's limb column, which holds X mod 2^(32 LB) in rows
 // [0, LB): relinearisation rounding / rescale / additions / centring per
 // EpiArgs, then the store of epi.out_limbs limbs.
-__device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, int LB, const EpiArgs& epi, int poly,
-                                          int b, int n, int N, uint32_t* __restrict__ out, size_t out_pstride,
-                                          size_t out_bstride) {
+__device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, int cstride, int LB, const EpiArgs& epi,
+                                          int poly, int b, int n, int N, uint32_t* __restrict__ out,
+                                          size_t out_pstride, size_t out_bstride) {
 
   const int ob = epi.item_bits ? __ldg(epi.item_bits + b) : epi.out_bits;
   int nl = LB;  // live limbs in the column
   if (epi.kind == Epi::kRelin) {
-    if (epi.shift > 0) col_add_pow2(sv, tid, LB, epi.shift - 1);
+    if (epi.shift > 0) col_add_pow2(sv, tid, cstride, LB, epi.shift - 1);
     const int nz = (ob + 31) >> 5;
-    col_shift_right(sv, tid, LB, nz, epi.shift);
+    col_shift_right(sv, tid, cstride, LB, nz, epi.shift);
     nl = nz;
   } else if (epi.kind == Epi::kAddSmall && epi.negate) {
     uint32_t c = 1;
@@ -109,10 +109,10 @@ __device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, in
 
   int fb = ob;  // bits of the final modulus
   if (epi.kind == Epi::kRelin && epi.k2 > 0) {
-    col_add_pow2(sv, tid, nl, epi.k2 - 1);
+    col_add_pow2(sv, tid, cstride, nl, epi.k2 - 1);
     fb = ob - epi.k2;
     const int nf = (fb + 31) >> 5;
-    col_shift_right(sv, tid, nl, nf, epi.k2);
+    col_shift_right(sv, tid, cstride, nl, nf, epi.k2);
     for (int l = 0; l < nf; ++l) COL(l) &= limb_mask(l, fb);
     nl = nf;
   }
@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
                                                         const uint32_t* __restrict__ mprod) {
   extern __shared__ uint32_t sv[];  // [rows][kCrtThreads], one column per thread
   const int tid = threadIdx.x;
+  constexpr int cstride = kCrtThreads;
   const int n = blockIdx.x * blockDim.x + tid;
   if (n >= N) return;  // columns are private: no block-wide barrier below
   const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
   // 4. epilogue on the column
 #pragma unroll
   for (int l = 0; l < LB; ++l) COL(l) = X[l];
-  crt_epilogue(sv, tid, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
+  crt_epilogue(sv, tid, kCrtThreads, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
 }
 
 
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
   extern __shared__ uint32_t sv[];  // [rows][kCrtThreads] y_0..y_{r-1}, kappa (later the limb column),
                                     // then [2][r+1][8] digit columns of the current block
   const int tid = threadIdx.x;
+  constexpr int cstride = kCrtThreads;
   const int rows = (r + 1) > (LB + 2) ? (r + 1) : (LB + 2);
   uint32_t* cbase = sv + (size_t)rows * kCrtThreads;
   const int n = blockIdx.x * blockDim.x + tid;
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
   // 3. epilogue on the limb column (the y rows are dead)
 #pragma unroll
   for (int l = 0; l < LB; ++l) COL(l) = X[l];
-  crt_epilogue(sv, tid, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
+  crt_epilogue(sv, tid, kCrtThreads, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
 }
 
 template <int LB>

@@ -276,7 +276,41 @@ __global__ void k_key_combine(const uint32_t* __restrict__ t, int Lt, const int3
   }
 }
 
+// b_0 += value 2^shift (mod 2^bits) for each ciphertext of the batch (addconst)
+__global__ void k_add_const(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t value, int shift,
+                            int L, int bits, int N, int cnum) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cnum) return;
+  const size_t base = (size_t)c * 2 * L * N;  // coefficient 0 of poly 0
+  const int sl = shift >> 5, sb = shift & 31;
+  const uint64_t v = (uint64_t)value;
+  const uint32_t ext = value < 0 ? 0xFFFFFFFFu : 0u;
+  // limb j of value << shift: bits of the sign-extended value
+  uint32_t carry = 0;
+  for (int l = 0; l < L; ++l) {
+    const int a = l - sl;
+    auto word = [&](int w) -> uint32_t {
+      if (w < 0) return 0u;
+      if (w == 0) return (uint32_t)v;
+      if (w == 1) return (uint32_t)(v >> 32);
+      return ext;
+    };
+    const uint32_t hi = word(a), lo = word(a - 1);
+    const uint32_t add = sb ? __funnelshift_l(lo, hi, sb) : hi;
+    const uint64_t s = (uint64_t)in[base + (size_t)l * N] + add + carry;
+    carry = (uint32_t)(s >> 32);
+    out[base + (size_t)l * N] = (uint32_t)s & mask_of(l, bits);
+  }
+}
+
 static dim3 limb_grid(int N, int y, int threads) { return dim3((N + threads - 1) / threads, y); }
+
+int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, int shift, int logQ,
+                     int cnum, cudaStream_t st) {
+  ProfScope ps(ctx, FHE_K_LIMB, 1, st);
+  k_add_const<<<(cnum + 127) / 128, 128, 0, st>>>(in, out, value, shift, limbs_for_bits(logQ), logQ, ctx->N, cnum);
+  return FHE_OK;
+}
 
 int launch_rescale(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t* out, int k, int npolys,
                    cudaStream_t st) {

@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--workload", default="ns", choices=["ns", "batched", "serving"],
                     help="ns: the headline N=2^16 logQ=1200 batch; batched: 512 uneven pairs, graph vs per-op")
-    ap.add_argument("--crt", default="direct", choices=["direct", "garner"],
-                    help="RNS->limb reconstruction: exact CRT with rounded quotient, or Garner mixed radix")
+    ap.add_argument("--crt", default="direct", choices=["direct", "garner", "int"],
+                    help="RNS->limb reconstruction: exact CRT with rounded quotient (dense sum on the tensor "
+                         "cores), Garner mixed radix, or the exact CRT on the integer pipe only")
     return ap.parse_args()
 
 
@@ -181,9 +182,19 @@ def crt_slots(r: int, out_limbs: int) -> int:
     return digits + horner
 
 
-def step_work(fhe, cnum: int, garner: bool) -> dict:
-    """Algorithmic IMAD-pipe slots per step, by kernel class."""
-    cs = crt_slots if garner else crt_slots_direct
+def crt_flops_tc(r: int, out_limbs: int) -> int:
+    """Tensor-core FLOPs of one direct-CRT reconstruction (one coefficient), algorithmic count.
+
+    The dense sum over r + 1 terms (y_i and kappa) times out_limbs limbs, in
+    byte digits: 4 (r + 1) x 4 out_limbs multiply-adds, 2 FLOPs each (no
+    padding of K to 16 or of the output columns to 16 counted).
+    """
+    return 2 * 4 * (r + 1) * 4 * out_limbs
+
+
+def step_work(fhe, cnum: int, crt_mode: str) -> dict:
+    """Algorithmic work per step, by kernel class: IMAD-pipe slots, or tensor FLOPs for the tensor-core CRT."""
+    cs = {"garner": crt_slots, "int": crt_slots_direct, "direct": crt_flops_tc}[crt_mode]
     N = 1 << LOGN
     L = (LOGQ + 31) // 32
     rt = fhe.fhe_primes_for_bound(LOGN + 2 * LOGQ + 1)
@@ -198,6 +209,14 @@ def step_work(fhe, cnum: int, garner: bool) -> dict:
         "pointwise": cnum * N * (3 * rt + 2 * rk) * 6,
         "primes": {"tensor": rt, "keyswitch": rk},
     }
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
 
 
 def read_traffic(kernel: str):
@@ -242,7 +261,7 @@ def run_ours(args):
     N = 1 << LOGN
     L = fhe.limbs(LOGQ)
     g = fs.rng(77 + rank)
-    crt = fhe.FHE_CRT_GARNER if args.crt == "garner" else fhe.FHE_CRT_DIRECT
+    crt = {"garner": fhe.FHE_CRT_GARNER, "int": fhe.FHE_CRT_DIRECT_INT, "direct": fhe.FHE_CRT_DIRECT}[args.crt]
     ctx = fhe.Context(LOGN, LOGQ, LOGP, crt=crt)
     ctx.keygen(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, LOGQ), fs.gaussian(g, (), N),
                fs.uniform_limbs(g, (), N, LOGQ + LOGP), fs.gaussian(g, (), N))
@@ -350,14 +369,23 @@ def run_ours(args):
             lat.append(s0.elapsed_time(s1))
     lat.sort()
 
-    work = step_work(fhe, cnum, args.crt == "garner")
+    work = step_work(fhe, cnum, args.crt)
     times = {k: v[1] for k, v in prof.items()}
     dominant = max((k for k in times if k in work), key=lambda k: times[k])
-    total_slots = work[dominant] * args.steps
-    achieved = total_slots / (times[dominant] / 1e3) / 1e12  # Tslot/s
-    peak = SM_COUNT * IMAD_SLOTS_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    total_work = work[dominant] * args.steps
+    achieved = total_work / (times[dominant] / 1e3) / 1e12  # Tslot/s or TFLOP/s
     nlaunch_dom = prof[dominant][0]
     traffic = read_traffic(dominant)
+    if dominant == "crt" and args.crt == "direct":
+        peaks = measured_peaks()
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_basis": ("measured dense bf16 (= fp16 nominal rate), sustained, MEASURED_PEAKS.json"
+                               if peaks.get("bf16_tflops_sustained") else "fallback sustained bf16 1.7 PFLOP/s")}
+    else:
+        peak = SM_COUNT * IMAD_SLOTS_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "Tslot/s",
+                "peak_basis": f"{SM_COUNT} SMs x {IMAD_SLOTS_PER_CLK} IMAD-pipe slots/clk x {SM_MAX_MHZ} MHz"}
 
     result = {
         "metric": METRIC, "value": value, "unit": "ct/s", "n_gpus": world, "steps": args.steps,
@@ -371,10 +399,9 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "ct/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "Tslot/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": f"{SM_COUNT} SMs x {IMAD_SLOTS_PER_CLK} IMAD-pipe slots/clk x {SM_MAX_MHZ} MHz",
-                     "launches": nlaunch_dom},
+        "roofline": {"bound": roof["bound"], "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "unit": roof["unit"], "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": roof["peak_basis"], "launches": nlaunch_dom},
         "kernels": {k: {"launches": n, "ms": t, "share": t / max(1e-9, sum(times.values()))}
                     for k, (n, t) in prof.items()},
         "clocks": clk,

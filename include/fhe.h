@@ -83,17 +83,20 @@ typedef struct {
   int32_t logQ;   /* CKKS: top modulus Q = 2^logQ (Sec. 6 log q).  BGV: the bit length
                      of the top modulus Q_L = q0 r^L (checked)                         */
   int32_t logP;   /* special modulus P = 2^logP of the switching keys                 */
-  int32_t crt;    /* RNS -> limb reconstruction: FHE_CRT_DIRECT (0, default) or
-                     FHE_CRT_GARNER (1, the mixed-radix form of Sec. 2 Eq. garner_mrc);
-                     both give identical results                                    */
+  int32_t crt;    /* RNS -> limb reconstruction: FHE_CRT_DIRECT (0, default),
+                     FHE_CRT_GARNER (1, the mixed-radix form of Sec. 2 Eq. garner_mrc)
+                     or FHE_CRT_DIRECT_INT (2); all give identical results          */
   int32_t bgv_levels; /* BGV: top level L of the chain Q_l = q0 r^l (0 for CKKS)      */
   uint32_t t;         /* BGV: plaintext modulus, odd, 3 <= t < 2^31 (0 for CKKS)      */
   uint64_t bgv_q0;    /* BGV: odd, = 1 mod t                                         */
   uint64_t bgv_r;     /* BGV: odd, = 1 mod t, 2^8 < r < 2^62                           */
 } fhe_params;
 
-#define FHE_CRT_DIRECT 0 /* exact CRT sum with a rounded quotient (Halevi-Polyakov-Shoup) */
-#define FHE_CRT_GARNER 1 /* Garner's mixed-radix conversion, digits in the nested order   */
+#define FHE_CRT_DIRECT 0     /* exact CRT sum with a rounded quotient (Halevi-Polyakov-Shoup);
+                                the dense sum runs on the fp16 tensor cores as a byte-digit
+                                GEMM wherever r + 1 <= 255 and N is a multiple of 64      */
+#define FHE_CRT_GARNER 1     /* Garner's mixed-radix conversion, digits in the nested order   */
+#define FHE_CRT_DIRECT_INT 2 /* the direct CRT with its dense sum on the integer pipe only  */
 
 typedef struct {
   uint32_t* data; /* device, uint32_t[cnum][2][L][N], L = ceil(logQ/32)               */
@@ -119,7 +122,10 @@ int fhe_ctx_destroy(fhe_ctx* ctx);
 /* Message of the last failed call on this thread ("" if none). */
 const char* fhe_last_error(void);
 
-/* Synchronise the device and report any pending asynchronous CUDA error. */
+/* Synchronise the device and report any pending asynchronous CUDA error;
+ * FHE_ETIMEOUT if a kernel's bounded wait (the tensor-core reconstruction's
+ * pipeline barriers) gave up since the last call, in which case the results
+ * enqueued meanwhile are invalid. */
 int fhe_sync(fhe_ctx* ctx);
 
 /* Bytes of a ciphertext batch: cnum * 2 * ceil(logQ/32) * 2^logN * 4. */

@@ -381,7 +381,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   if ((p->scheme != FHE_SCHEME_CKKS && p->scheme != FHE_SCHEME_BGV) || p->logN < 3 || p->logN > kMaxLogN ||
       p->logQ < 1 || p->logP < 1 ||
       p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr) ||
-      (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER)) {
+      (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER && p->crt != FHE_CRT_DIRECT_INT)) {
     set_error("ctx_create: parameters out of range (logN %d, logQ %d, logP %d)", p->logN, p->logQ, p->logP);
     return FHE_EINVAL;
   }
@@ -438,6 +438,10 @@ int fhe_sync(fhe_ctx* ctx) {
   (void)ctx;
   FHE_CHECK_CUDA(cudaDeviceSynchronize());
   FHE_CHECK_CUDA(cudaGetLastError());
+  if (read_dev_status()) {
+    set_error("a bounded device-side wait gave up (results of the preceding work are invalid)");
+    return FHE_ETIMEOUT;
+  }
   return FHE_OK;
 }
 

@@ -103,7 +103,15 @@ struct fhe_ctx {
   uint32_t* d_crt_negm = nullptr; // [R+1][kMaxLimbs] (-M_r) mod 2^(32 kMaxLimbs)
   float* d_invq = nullptr;        // [R] 1/q_i rounded to fp32
   uint32_t* d_crt_dig = nullptr;  // per r: [r+1][kCrtDigits] 24-bit digits of (M_r/q_i) mod 2^4096, last row -M_r
-  int crt_mode = 0;               // 0 direct CRT, 1 Garner (Eq. garner_mrc)
+  // the same dense product on the tcgen05 tensor cores: per r, the B operand [P][K] in f16, the
+  // balanced byte digits of (M_r/q_i) and -M_r Toeplitz-shifted by the digit index a of y_i
+  // (B[p][4i + a] = c_{i,p-a}); K in chunks of 64, each chunk [p/8][k/8][p%8][k%8] (K-major core
+  // matrices, no swizzle) for p < 16 crt_tc_mt; set r starts at crt_tc_off[r] (f16 elements)
+  uint16_t* d_crt_tc = nullptr;
+  std::vector<size_t> crt_tc_off;
+  int crt_tc_mt = 0;              // output byte columns covered, in 16s
+  int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 1 Garner (Eq. garner_mrc),
+                                  // 2 direct CRT on the integer pipe only
   // BGV (scheme FHE_SCHEME_BGV): chain constants per level, and bit lengths of Q_l
   fhe::BgvLevel* d_bgv_levels = nullptr;
   fhe::BgvConsts* d_bgv_consts = nullptr;
@@ -235,6 +243,7 @@ struct EpiArgs {
 };
 // in: [nbatch][npoly][r][N] (poly stride in_pstride, batch in_bstride);
 // out: [nbatch][npoly][out_limbs][N] (strides out_pstride, out_bstride).
+unsigned int read_dev_status();  // nonzero (then cleared) after a bounded device wait gave up
 int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, size_t in_bstride, int r, int npoly,
                   int nbatch, uint32_t* out, size_t out_pstride, size_t out_bstride, const EpiArgs& epi,
                   cudaStream_t st);

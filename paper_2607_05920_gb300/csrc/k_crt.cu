@@ -57,10 +57,12 @@ __device__ __forceinline__ void col_shift_right(uint32_t* sv, int tid, int cstri
 
 // Epilogue on the thread's limb column, which holds X mod 2^(32 LB) in rows
 // [0, LB): relinearisation rounding / rescale / additions / centring per
-// EpiArgs, then the store of epi.out_limbs limbs.
+// EpiArgs, then the store of epi.out_limbs limbs.  add_s, when given, holds
+// the addend limbs already staged in shared memory (limb l at l * add_sstride).
 __device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, int cstride, int LB, const EpiArgs& epi,
                                           int poly, int b, int n, int N, uint32_t* __restrict__ out,
-                                          size_t out_pstride, size_t out_bstride) {
+                                          size_t out_pstride, size_t out_bstride,
+                                          const uint32_t* add_s = nullptr, int add_sstride = 0) {
 
   const int ob = epi.item_bits ? __ldg(epi.item_bits + b) : epi.out_bits;
   int nl = LB;  // live limbs in the column
@@ -82,7 +84,7 @@ __device__ __noinline__ void crt_epilogue(uint32_t* __restrict__ sv, int tid, in
     const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n;
     uint32_t c = 0;
     for (int l = 0; l < nlo; ++l) {
-      const uint32_t a = l < epi.add_limbs ? __ldg(ad + (size_t)l * N) : 0u;
+      const uint32_t a = l < epi.add_limbs ? (add_s ? add_s[(size_t)l * add_sstride] : __ldg(ad + (size_t)l * N)) : 0u;
       const uint32_t x = l < nl ? COL(l) : 0u;
       const uint64_t s = (uint64_t)x + a + c;
       COL(l) = (uint32_t)s;
@@ -332,6 +334,322 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
   crt_epilogue(sv, tid, kCrtThreads, LB, epi, poly, b, n, N, out, out_pstride, out_bstride);
 }
 
+// ------------------------------------------------- direct CRT, tensor cores
+// The dense part of the direct CRT, sum_i y_i C_i (C_i = M/q_i, and kappa
+// times C_r = -M), as an fp16 GEMM on the tcgen05 tensor cores.  y_i and C_i
+// are split into balanced bytes (digits in [-128, 128]), so every product is
+// an integer of magnitude <= 2^14 and a column sum over 4 (r + 1) <= 1020
+// terms stays below 2^24: the fp32 accumulator is exact.  Output byte column
+// p is S_p = sum_{i,a} d_{i,a} c_{i,p-a}: D[128 coefficients][P] =
+// A[128][K] B[P][K]^T with K = 4 i + a, the byte digits of y_i in A and the
+// Toeplitz-shifted digits c_{i,p-a} in B (host-built, build_crt_tc).
+//
+// One CTA = 128 coefficients = the MMA's M = the 128 TMEM lanes, so thread t
+// finds coefficient t's column sums in its own TMEM lane.  Warp roles:
+//   warps 0-3  y_i = [x_i (M/q_i)^-1]_{q_i} and kappa from the staged
+//              residues, written as f16 digits into the A stage; after the
+//              last MMA: S_p from TMEM, carried into 32-bit limbs, epilogue;
+//   warp 4     bulk copies (TMA engine): residue rows, B chunks, the addend;
+//   warp 5     TMEM allocation and the MMA issue (one thread), committing
+//              each stage back to its producer's mbarrier.
+// K runs in chunks of 64 (16 primes); every wait is bounded and reports a
+// timeout through fhe_dev_status.
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 192;
+constexpr int kTcNX = 3;                    // residue stages
+constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficients
+constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
+constexpr int kTcHead = 1024;               // mbarriers + TMEM address
+
+__device__ unsigned int g_fhe_dev_status = 0;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Waits for the phase of the given parity to complete; gives up after a
+// bounded number of polls, records the timeout and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicOr(&g_fhe_dev_status, 1u);
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between 8-row groups.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Balanced bytes of y < 2^31 as two f16x2 registers {d0, d1}, {d2, d3}:
+// e = y + 0x808080, d_a = byte_a(e) - 128 for a < 3, d_3 = byte_3(e) <= 128.
+// A byte b is placed under the f16 exponent of 1024 (bits 0x6400 | b = 1024 + b),
+// then 1152 (or 1024) is subtracted exactly.
+__device__ __forceinline__ void y_digits(uint32_t y, uint32_t& lo, uint32_t& hi) {
+  const uint32_t e = y + 0x00808080u;
+  const uint32_t l = __byte_perm(e, 0x64646464u, 0x5140);
+  const uint32_t h = __byte_perm(e, 0x64646464u, 0x5342);
+  asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(lo) : "r"(l), "r"(0x64806480u));
+  asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(hi) : "r"(h), "r"(0x64006480u));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_crt_tc(const uint32_t* __restrict__ in, size_t in_pstride, size_t in_bstride, int r, int npoly,
+             uint32_t* __restrict__ out, size_t out_pstride, size_t out_bstride, EpiArgs epi, int N,
+             const uint32_t* __restrict__ qtab, const uint2* __restrict__ cinv, const float* __restrict__ invq,
+             const uint16_t* __restrict__ bmat, int pmax, int MT, int tmem_cols, int stage_add) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int P = 16 * MT;
+  const int KS = (r + 4) >> 2;          // k-steps of 16 over the 4 (r + 1) digits
+  const int nch = (KS + 3) >> 2;        // chunks of 4 k-steps (16 primes)
+  const uint32_t bstage = (uint32_t)P * 128u;
+  uint8_t* X = smem + kTcHead;
+  uint8_t* A = X + kTcNX * kTcXStage;
+  uint8_t* B = A + 2 * kTcAStage;
+  uint8_t* ADD = B + 2 * bstage;
+  const uint32_t bar0 = smem_addr(smem);
+  // mbarriers, 8 bytes each
+  auto x_full = [&](int s) { return bar0 + 8u * s; };
+  auto x_empty = [&](int s) { return bar0 + 8u * (3 + s); };
+  auto a_full = [&](int s) { return bar0 + 8u * (6 + s); };
+  auto a_empty = [&](int s) { return bar0 + 8u * (8 + s); };
+  auto b_full = [&](int s) { return bar0 + 8u * (10 + s); };
+  auto b_empty = [&](int s) { return bar0 + 8u * (12 + s); };
+  const uint32_t acc_full = bar0 + 8u * 14, add_full = bar0 + 8u * 15;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 256);
+
+  const int n0 = blockIdx.x * kTcRows;
+  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
+  stage_add = stage_add && poly < epi.add_polys;  // only polynomials that take an addend have one
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcNX; ++s) {
+      mbar_init(x_full(s), 1);
+      mbar_init(x_empty(s), kTcRows);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(a_full(s), kTcRows);
+      mbar_init(a_empty(s), 1);
+      mbar_init(b_full(s), 1);
+      mbar_init(b_empty(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(add_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if ((tid & 31) == 0) {
+      // producer: the addend limbs (epilogue), then per chunk the residue rows and the B chunk
+      if (stage_add) {
+        const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0;
+        mbar_expect_tx(add_full, (uint32_t)epi.add_limbs * 512u);
+        for (int l = 0; l < epi.add_limbs; ++l) bulk_g2s(smem_addr(ADD + 512 * l), ad + (size_t)l * N, 512u, add_full);
+      }
+      const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n0;
+      for (int c = 0; c < nch; ++c) {
+        const int sx = c % kTcNX;
+        if (c >= kTcNX && !mbar_wait(x_empty(sx), (uint32_t)((c / kTcNX) - 1) & 1u)) break;
+        const int rows = max(0, min(16, r - 16 * c));
+        mbar_expect_tx(x_full(sx), (uint32_t)rows * 512u);
+        for (int j = 0; j < rows; ++j)
+          bulk_g2s(smem_addr(X + sx * kTcXStage + 512 * j), src + (size_t)(16 * c + j) * N, 512u, x_full(sx));
+        const int sb = c & 1;
+        if (c >= 2 && !mbar_wait(b_empty(sb), (uint32_t)((c >> 1) - 1) & 1u)) break;
+        mbar_expect_tx(b_full(sb), bstage);
+        bulk_g2s(smem_addr(B + sb * bstage), bmat + (size_t)c * pmax * 64, bstage, b_full(sb));
+      }
+    }
+  } else if (warp == 5) {
+    if ((tid & 31) == 0) {
+      // MMA issue: D[128][P] += A_chunk B_chunk^T, output columns in pieces of at most 256
+      const int nsplit = (MT + 15) / 16;
+      for (int c = 0; c < nch; ++c) {
+        const int s = c & 1;
+        const uint32_t par = (uint32_t)(c >> 1) & 1u;
+        if (!mbar_wait(a_full(s), par) || !mbar_wait(b_full(s), par)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t abase = smem_addr(A + s * kTcAStage), bbase = smem_addr(B + s * bstage);
+        const int nks = min(4, KS - 4 * c);
+        for (int ks = 0; ks < nks; ++ks) {
+          for (int sp = 0; sp < nsplit; ++sp) {
+            const int m0 = sp * MT / nsplit, m1 = (sp + 1) * MT / nsplit;
+            const uint32_t n = 16u * (uint32_t)(m1 - m0);
+            const uint32_t idesc = (1u << 4) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+            const uint64_t da = tc_desc(abase + 256u * ks, 128u, 1024u);
+            const uint64_t db = tc_desc(bbase + (uint32_t)(2 * m0) * 1024u + 256u * ks, 128u, 1024u);
+            tc_mma(tmem + 16u * (uint32_t)m0, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        tc_commit(a_empty(s));
+        tc_commit(b_empty(s));
+      }
+      tc_commit(acc_full);
+    }
+  } else {
+    // rows: coefficient n0 + tid
+    const int t = tid;
+    float fs = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; ++c) {
+      const int sx = c % kTcNX, sa = c & 1;
+      ok = mbar_wait(x_full(sx), (uint32_t)(c / kTcNX) & 1u);
+      if (ok && c >= 2) ok = mbar_wait(a_empty(sa), (uint32_t)((c >> 1) - 1) & 1u);
+      if (!ok) break;
+      const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage);
+      uint8_t* arow = A + sa * kTcAStage + (t >> 3) * 1024 + (t & 7) * 16;
+#pragma unroll 2
+      for (int jp = 0; jp < 8; ++jp) {
+        uint32_t d[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = 2 * jp + u, i = 16 * c + j;
+          uint32_t y = 0;
+          if (i < r) {
+            const uint2 ci = __ldg(cinv + i);
+            y = shoup_mul(xs[j * kTcRows + t], ci.x, ci.y, __ldg(qtab + i));
+            fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
+          } else if (i == r) {
+            y = (uint32_t)__float2int_rn(fs);  // kappa: every y_i is in fs by now
+          }
+          y_digits(y, d[2 * u], d[2 * u + 1]);
+        }
+        *reinterpret_cast<uint4*>(arow + jp * 128) = make_uint4(d[0], d[1], d[2], d[3]);
+      }
+      mbar_arrive(x_empty(sx));
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive(a_full(sa));
+    }
+    if (ok) ok = mbar_wait(acc_full, 0);
+    ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld below is warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // column sums -> limbs (limb column over the dead A/B stages), then the epilogue
+    uint32_t* col = reinterpret_cast<uint32_t*>(A);
+    if (ok) {
+      long long carry = 0;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int m = 0; m < MT; ++m) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(lane_base + 16u * (uint32_t)m));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const long long val = carry + (long long)__float2int_rn(__uint_as_float(v[4 * q])) +
+                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 1])) * 256LL +
+                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 2])) * 65536LL +
+                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 3])) * 16777216LL;
+          col[(size_t)(4 * m + q) * kTcRows + t] = (uint32_t)val;
+          carry = val >> 32;
+        }
+      }
+      if (stage_add) ok = mbar_wait(add_full, 0);
+      if (ok)
+        crt_epilogue(col, t, kTcRows, 4 * MT, epi, poly, b, n0 + t, N, out, out_pstride, out_bstride,
+                     stage_add ? reinterpret_cast<const uint32_t*>(ADD) + t : nullptr, kTcRows);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+// Shared memory of k_crt_tc: header, residue stages, two A stages, two B
+// stages of P x 64 f16, and the staged addend limbs.
+static size_t tc_smem_bytes(int MT, int add_rows) {
+  return (size_t)kTcHead + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage + 2 * (size_t)MT * 16 * 128 +
+         (size_t)add_rows * 512;
+}
+
+// Runs the tensor-core form when it applies; returns 1 if launched, 0 if the
+// caller must use the integer form (nothing enqueued).
+static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
+                     uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, int need, cudaStream_t st) {
+  const int N = ctx->N;
+  const int MT = (need + 3) / 4;
+  if (!ctx->d_crt_tc || r + 1 > 255 || N % kTcRows != 0 || MT > ctx->crt_tc_mt || (ip & 3) || (ib & 3) ||
+      ((uintptr_t)in & 15))
+    return 0;
+  int stage_add = 0;
+  if (epi.add && epi.add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
+      !(epi.add_bstride & 3))
+    stage_add = 1;
+  if (epi.add && !stage_add) return 0;
+  const size_t smem = tc_smem_bytes(MT, stage_add ? epi.add_limbs : 0);
+  if (smem > 227 * 1024) return 0;
+  int cols = 32;
+  while (cols < 16 * MT) cols <<= 1;
+  static thread_local int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    configured_dev = ctx->device;
+  }
+  dim3 grid(N / kTcRows, npoly * nbatch);
+  ProfScope ps(ctx, FHE_K_CRT, 1, st);
+  const size_t off = (size_t)r * (r - 1) / 2;
+  k_crt_tc<<<grid, kTcThreads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q, ctx->d_crt_inv + off,
+                                           ctx->d_invq, ctx->d_crt_tc + ctx->crt_tc_off[r], 16 * ctx->crt_tc_mt, MT,
+                                           cols, stage_add);
+  return 1;
+}
+
+// Device status word: nonzero after a bounded wait gave up.  Read and cleared.
+unsigned int read_dev_status() {
+  unsigned int v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fhe_dev_status, sizeof(v)) != cudaSuccess) return 0;
+  if (v) cudaMemcpyToSymbol(g_fhe_dev_status, &z, sizeof(z));
+  return v;
+}
+
 template <int LB>
 static int direct_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
                          uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, cudaStream_t st) {
@@ -382,6 +700,9 @@ int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, siz
     set_error("garner: %d limbs exceed %d", need, kMaxLimbs);
     return FHE_EINVAL;
   }
+  if (ctx->crt_mode == 0 &&
+      tc_launch(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, epi, need, st))
+    return FHE_OK;
 #define FHE_GARNER_CASE(B)                                                                                       \
   if (need <= B)                                                                                                 \
     return ctx->crt_mode == 1                                                                                    \

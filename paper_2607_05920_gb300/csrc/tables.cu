@@ -187,6 +187,68 @@ static T* upload(fhe_ctx* ctx, const std::vector<T>& h) {
   return d;
 }
 
+// fp16 bit pattern of a small integer, |v| <= 2048 (exact).
+static uint16_t half_of_int(int v) {
+  if (v == 0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  const unsigned a = (unsigned)(v < 0 ? -v : v);
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;
+  const unsigned mant = (a << (10 - e)) & 0x3FFu;
+  return (uint16_t)(sign | (unsigned)((e + 15) << 10) | mant);
+}
+
+// Balanced base-256 digits c_p in [-128, 127] of x mod 2^(32 kMaxLimbs):
+// sum_p c_p 256^p = x (mod 2^(32 kMaxLimbs)); the carry out of the top is dropped.
+static void balanced_bytes(const uint32_t* limbs, int8_t* out) {
+  int carry = 0;
+  for (int p = 0; p < 4 * kMaxLimbs; ++p) {
+    const int v = (int)((limbs[p >> 2] >> (8 * (p & 3))) & 0xFFu) + carry;
+    carry = v >= 128 ? 1 : 0;
+    out[p] = (int8_t)(v - 256 * carry);
+  }
+}
+
+// Tensor-core form of the direct CRT's dense product (k_crt_tc).  Output
+// byte column p of sum_i y_i C_i (C_i = M_r/q_i, C_r = -M_r with y_r = kappa)
+// is S_p = sum_i sum_a d_{i,a} c_{i,p-a}, d_{i,a} the balanced bytes of y_i,
+// c_{i,.} those of C_i: a GEMM with K = 4 i + a and the B operand
+// B[p][4 i + a] = c_{i,p-a}, stored per chunk of 64 k as K-major core
+// matrices (8 rows x 8 f16) in the order [p/8][k/8][p%8][k%8].
+static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const std::vector<uint32_t>& negm) {
+  const int R = ctx->R;
+  const int lmax = (R + 4 < kMaxLimbs) ? R + 4 : kMaxLimbs;
+  const int MT = (lmax + 3) / 4;
+  const int P = 16 * MT;
+  ctx->crt_tc_mt = MT;
+  ctx->crt_tc_off.assign(R + 1, 0);
+  size_t total = 0;
+  for (int r = 1; r <= R; ++r) {
+    ctx->crt_tc_off[r] = total;
+    total += (size_t)((r + 16) / 16) * P * 64;
+  }
+  std::vector<uint16_t> mat(total, 0);
+  std::vector<int8_t> dig((size_t)(R + 1) * 4 * kMaxLimbs);
+  uint16_t h16[256];
+  for (int v = -128; v < 128; ++v) h16[v + 128] = half_of_int(v);
+  for (int r = 1; r <= R; ++r) {
+    const size_t off = (size_t)r * (r - 1) / 2;
+    for (int i = 0; i < r; ++i) balanced_bytes(&qhat[(off + i) * kMaxLimbs], &dig[(size_t)i * 4 * kMaxLimbs]);
+    balanced_bytes(&negm[(size_t)r * kMaxLimbs], &dig[(size_t)r * 4 * kMaxLimbs]);
+    const int nch = (r + 16) / 16;
+    uint16_t* base = mat.data() + ctx->crt_tc_off[r];
+    for (int c = 0; c < nch; ++c)
+      for (int p = 0; p < P; ++p)
+        for (int k = 0; k < 64; ++k) {
+          const int kg = 64 * c + k, i = kg >> 2, a = kg & 3, pa = p - a;
+          if (i > r || pa < 0) continue;
+          base[(size_t)c * P * 64 + ((size_t)(p >> 3) * 8 + (k >> 3)) * 64 + (p & 7) * 8 + (k & 7)] =
+              h16[dig[(size_t)i * 4 * kMaxLimbs + pa] + 128];
+        }
+  }
+  return (ctx->d_crt_tc = upload(ctx, mat)) ? FHE_OK : FHE_ENOMEM;
+}
+
 int build_tables(fhe_ctx* ctx) {
   const int N = ctx->N, logN = ctx->prm.logN, R = ctx->R;
   const auto& gp = global_primes();
@@ -322,6 +384,7 @@ int build_tables(fhe_ctx* ctx) {
     digits_of(&negm[(size_t)r * kMaxLimbs], &dig[(base + r) * kCrtDigits]);
   }
   if (!(ctx->d_crt_dig = upload(ctx, dig))) return FHE_ENOMEM;
+  if (build_crt_tc(ctx, qhat, negm) != FHE_OK) return FHE_ENOMEM;
   if (!(ctx->d_crt_qhat = upload(ctx, qhat)) || !(ctx->d_crt_inv = upload(ctx, crt_inv)) ||
       !(ctx->d_crt_negm = upload(ctx, negm)) || !(ctx->d_invq = upload(ctx, invq)))
     return FHE_ENOMEM;

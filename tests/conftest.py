@@ -26,3 +26,15 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _device_waits_completed(request):
+    """After every GPU test: no bounded device-side wait gave up (fhe_sync reports FHE_ETIMEOUT)."""
+    yield
+    if "gpu" not in request.keywords:
+        return
+    import paper_2607_05920_gb300 as fhe
+
+    rc = fhe.lib.fhe_sync(None)
+    assert rc == 0, f"fhe_sync after the test returned {rc}: {fhe.lib.fhe_last_error().decode()}"

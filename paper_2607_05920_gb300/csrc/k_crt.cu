@@ -344,22 +344,25 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
 // A[128][K] B[P][K]^T with K = 4 i + a, the byte digits of y_i in A and the
 // Toeplitz-shifted digits c_{i,p-a} in B (host-built, build_crt_tc).
 //
-// One CTA = 128 coefficients = the MMA's M = the 128 TMEM lanes, so thread t
-// finds coefficient t's column sums in its own TMEM lane.  Warp roles:
-//   warps 0-3  y_i = [x_i (M/q_i)^-1]_{q_i} and kappa from the staged
-//              residues, written as f16 digits into the A stage; after the
-//              last MMA: S_p from TMEM, carried into 32-bit limbs, epilogue;
-//   warp 4     bulk copies (TMA engine): residue rows, B chunks, the addend;
-//   warp 5     TMEM allocation and the MMA issue (one thread), committing
-//              each stage back to its producer's mbarrier.
-// K runs in chunks of 64 (16 primes); every wait is bounded and reports a
-// timeout through fhe_dev_status.
+// A tile = 128 coefficients of one polynomial = the MMA's M = the 128 TMEM
+// lanes.  The kernel is persistent (one CTA per SM walks the tiles) and warp
+// specialised, every hand-off an mbarrier:
+//   warps 0-3  (Y) y_i = [x_i (M/q_i)^-1]_{q_i} and kappa from the staged
+//              residues, as f16 digits into an A stage;
+//   warps 4-7  (E) per tile: S_p from the thread's own TMEM lane, carried into
+//              32-bit limbs, the accumulator released, then the epilogue;
+//   warp 8     bulk copies (TMA engine): residue rows, B chunks, the addend;
+//   warp 9     TMEM allocation and the MMA issue (one thread).
+// With P <= 256 two accumulators alternate, so the epilogue of one tile runs
+// under the GEMM of the next.  K runs in chunks of 64 (16 primes).  Every
+// wait is bounded and reports a timeout through fhe_sync.
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 320;
 constexpr int kTcNX = 3;                    // residue stages
 constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficients
 constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
 constexpr int kTcHead = 1024;               // mbarriers + TMEM address
+constexpr int kTcConst = 4096;              // per prime {q, cinv, cinv shoup, 1/q}
 
 __device__ unsigned int g_fhe_dev_status = 0;
 
@@ -424,35 +427,49 @@ __device__ __forceinline__ void y_digits(uint32_t y, uint32_t& lo, uint32_t& hi)
   asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(hi) : "r"(h), "r"(0x64006480u));
 }
 
+struct TcShape {
+  int r, MT, nblk, npoly, ntiles;  // primes, output m-tiles, 128-blocks per polynomial, tiles
+  int acc_cols, nacc;              // TMEM columns per accumulator, accumulators
+  int nadd;                        // staged addend buffers (0: the epilogue reads the addend from global)
+};
+
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_crt_tc(const uint32_t* __restrict__ in, size_t in_pstride, size_t in_bstride, int r, int npoly,
+    k_crt_tc(const uint32_t* __restrict__ in, size_t in_pstride, size_t in_bstride, TcShape sh,
              uint32_t* __restrict__ out, size_t out_pstride, size_t out_bstride, EpiArgs epi, int N,
              const uint32_t* __restrict__ qtab, const uint2* __restrict__ cinv, const float* __restrict__ invq,
-             const uint16_t* __restrict__ bmat, int pmax, int MT, int tmem_cols, int stage_add) {
+             const uint16_t* __restrict__ bmat, int pmax) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = sh.r, MT = sh.MT;
   const int P = 16 * MT;
-  const int KS = (r + 4) >> 2;          // k-steps of 16 over the 4 (r + 1) digits
-  const int nch = (KS + 3) >> 2;        // chunks of 4 k-steps (16 primes)
+  const int KS = (r + 4) >> 2;  // k-steps of 16 over the 4 (r + 1) digits
+  const int nch = (KS + 3) >> 2;  // chunks of 4 k-steps (16 primes)
   const uint32_t bstage = (uint32_t)P * 128u;
-  uint8_t* X = smem + kTcHead;
+  const int add_limbs = epi.add ? epi.add_limbs : 0;
+  uint4* CONST = reinterpret_cast<uint4*>(smem + kTcHead);
+  uint8_t* X = smem + kTcHead + kTcConst;
   uint8_t* A = X + kTcNX * kTcXStage;
   uint8_t* B = A + 2 * kTcAStage;
-  uint8_t* ADD = B + 2 * bstage;
+  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + 2 * bstage);
+  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (size_t)4 * MT * kTcRows);
   const uint32_t bar0 = smem_addr(smem);
-  // mbarriers, 8 bytes each
   auto x_full = [&](int s) { return bar0 + 8u * s; };
   auto x_empty = [&](int s) { return bar0 + 8u * (3 + s); };
   auto a_full = [&](int s) { return bar0 + 8u * (6 + s); };
   auto a_empty = [&](int s) { return bar0 + 8u * (8 + s); };
   auto b_full = [&](int s) { return bar0 + 8u * (10 + s); };
   auto b_empty = [&](int s) { return bar0 + 8u * (12 + s); };
-  const uint32_t acc_full = bar0 + 8u * 14, add_full = bar0 + 8u * 15;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 256);
-
-  const int n0 = blockIdx.x * kTcRows;
-  const int poly = blockIdx.y % npoly, b = blockIdx.y / npoly;
-  stage_add = stage_add && poly < epi.add_polys;  // only polynomials that take an addend have one
+  auto acc_full = [&](int s) { return bar0 + 8u * (14 + s); };
+  auto acc_empty = [&](int s) { return bar0 + 8u * (16 + s); };
+  auto add_full = [&](int s) { return bar0 + 8u * (18 + s); };
+  auto add_empty = [&](int s) { return bar0 + 8u * (20 + s); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 512);
+  auto tile_of = [&](int t, int& n0, int& poly, int& b) {
+    const int py = t / sh.nblk;
+    n0 = (t - py * sh.nblk) * kTcRows;
+    poly = py % sh.npoly;
+    b = py / sh.npoly;
+  };
 
   if (tid == 0) {
     for (int s = 0; s < kTcNX; ++s) {
@@ -464,14 +481,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(a_empty(s), 1);
       mbar_init(b_full(s), 1);
       mbar_init(b_empty(s), 1);
+      mbar_init(acc_full(s), 1);
+      mbar_init(acc_empty(s), kTcRows);
+      mbar_init(add_full(s), 1);
+      mbar_init(add_empty(s), kTcRows);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(add_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 5) {
+  for (int i = tid; i < r; i += kTcThreads) {
+    const uint2 ci = __ldg(cinv + i);
+    CONST[i] = make_uint4(__ldg(qtab + i), ci.x, ci.y, __float_as_uint(__ldg(invq + i)));
+  }
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
-                 "r"(tmem_cols)
+                 "r"(sh.acc_cols * sh.nacc)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -480,103 +503,136 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
-    if ((tid & 31) == 0) {
-      // producer: the addend limbs (epilogue), then per chunk the residue rows and the B chunk
-      if (stage_add) {
-        const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0;
-        mbar_expect_tx(add_full, (uint32_t)epi.add_limbs * 512u);
-        for (int l = 0; l < epi.add_limbs; ++l) bulk_g2s(smem_addr(ADD + 512 * l), ad + (size_t)l * N, 512u, add_full);
-      }
-      const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n0;
-      for (int c = 0; c < nch; ++c) {
-        const int sx = c % kTcNX;
-        if (c >= kTcNX && !mbar_wait(x_empty(sx), (uint32_t)((c / kTcNX) - 1) & 1u)) break;
-        const int rows = max(0, min(16, r - 16 * c));
-        mbar_expect_tx(x_full(sx), (uint32_t)rows * 512u);
-        for (int j = 0; j < rows; ++j)
-          bulk_g2s(smem_addr(X + sx * kTcXStage + 512 * j), src + (size_t)(16 * c + j) * N, 512u, x_full(sx));
-        const int sb = c & 1;
-        if (c >= 2 && !mbar_wait(b_empty(sb), (uint32_t)((c >> 1) - 1) & 1u)) break;
-        mbar_expect_tx(b_full(sb), bstage);
-        bulk_g2s(smem_addr(B + sb * bstage), bmat + (size_t)c * pmax * 64, bstage, b_full(sb));
+  if (warp == 8) {
+    if (lane == 0) {
+      // producer: per tile the addend limbs, per chunk the residue rows and the B chunk
+      int g = 0, tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
+        int n0, poly, b;
+        tile_of(t, n0, poly, b);
+        if (sh.nadd) {
+          const int s = tl % sh.nadd;
+          if (tl >= sh.nadd) ok = mbar_wait(add_empty(s), (uint32_t)((tl / sh.nadd) - 1) & 1u);
+          if (!ok) break;
+          const bool has = add_limbs > 0 && poly < epi.add_polys;
+          mbar_expect_tx(add_full(s), has ? (uint32_t)add_limbs * 512u : 0u);
+          if (has) {
+            const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0;
+            uint8_t* dst = ADD + (size_t)s * add_limbs * 512;
+            for (int l = 0; l < add_limbs; ++l)
+              bulk_g2s(smem_addr(dst + 512 * l), ad + (size_t)l * N, 512u, add_full(s));
+          }
+        }
+        const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n0;
+        for (int c = 0; c < nch; ++c, ++g) {
+          const int sx = g % kTcNX;
+          if (g >= kTcNX && !(ok = mbar_wait(x_empty(sx), (uint32_t)((g / kTcNX) - 1) & 1u))) break;
+          const int rows = max(0, min(16, r - 16 * c));
+          mbar_expect_tx(x_full(sx), (uint32_t)rows * 512u);
+          for (int j = 0; j < rows; ++j)
+            bulk_g2s(smem_addr(X + sx * kTcXStage + 512 * j), src + (size_t)(16 * c + j) * N, 512u, x_full(sx));
+          const int sb = g & 1;
+          if (g >= 2 && !(ok = mbar_wait(b_empty(sb), (uint32_t)((g >> 1) - 1) & 1u))) break;
+          mbar_expect_tx(b_full(sb), bstage);
+          bulk_g2s(smem_addr(B + sb * bstage), bmat + (size_t)c * pmax * 64, bstage, b_full(sb));
+        }
       }
     }
-  } else if (warp == 5) {
-    if ((tid & 31) == 0) {
+  } else if (warp == 9) {
+    if (lane == 0) {
       // MMA issue: D[128][P] += A_chunk B_chunk^T, output columns in pieces of at most 256
       const int nsplit = (MT + 15) / 16;
-      for (int c = 0; c < nch; ++c) {
-        const int s = c & 1;
-        const uint32_t par = (uint32_t)(c >> 1) & 1u;
-        if (!mbar_wait(a_full(s), par) || !mbar_wait(b_full(s), par)) break;
+      int g = 0, tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
+        const int ab = tl % sh.nacc;
+        if (tl >= sh.nacc && !(ok = mbar_wait(acc_empty(ab), (uint32_t)((tl / sh.nacc) - 1) & 1u))) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t abase = smem_addr(A + s * kTcAStage), bbase = smem_addr(B + s * bstage);
-        const int nks = min(4, KS - 4 * c);
-        for (int ks = 0; ks < nks; ++ks) {
-          for (int sp = 0; sp < nsplit; ++sp) {
-            const int m0 = sp * MT / nsplit, m1 = (sp + 1) * MT / nsplit;
-            const uint32_t n = 16u * (uint32_t)(m1 - m0);
-            const uint32_t idesc = (1u << 4) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-            const uint64_t da = tc_desc(abase + 256u * ks, 128u, 1024u);
-            const uint64_t db = tc_desc(bbase + (uint32_t)(2 * m0) * 1024u + 256u * ks, 128u, 1024u);
-            tc_mma(tmem + 16u * (uint32_t)m0, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        const uint32_t dbase = tmem + (uint32_t)(ab * sh.acc_cols);
+        for (int c = 0; c < nch; ++c, ++g) {
+          const int s = g & 1;
+          const uint32_t par = (uint32_t)(g >> 1) & 1u;
+          if (!(ok = mbar_wait(a_full(s), par)) || !(ok = mbar_wait(b_full(s), par))) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t abase = smem_addr(A + s * kTcAStage), bbase = smem_addr(B + s * bstage);
+          const int nks = min(4, KS - 4 * c);
+          for (int ks = 0; ks < nks; ++ks) {
+            for (int sp = 0; sp < nsplit; ++sp) {
+              const int m0 = sp * MT / nsplit, m1 = (sp + 1) * MT / nsplit;
+              const uint32_t n = 16u * (uint32_t)(m1 - m0);
+              const uint32_t idesc = (1u << 4) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+              const uint64_t da = tc_desc(abase + 256u * ks, 128u, 1024u);
+              const uint64_t db = tc_desc(bbase + (uint32_t)(2 * m0) * 1024u + 256u * ks, 128u, 1024u);
+              tc_mma(dbase + 16u * (uint32_t)m0, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            }
           }
+          tc_commit(a_empty(s));
+          tc_commit(b_empty(s));
         }
-        tc_commit(a_empty(s));
-        tc_commit(b_empty(s));
+        if (!ok) break;
+        tc_commit(acc_full(ab));
       }
-      tc_commit(acc_full);
+    }
+  } else if (warp < 4) {
+    // Y: digits of y_i (and kappa) for coefficient n0 + tid of every tile
+    const int t0 = tid;
+    int g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x) {
+      float fs = 0.f;
+      for (int c = 0; c < nch; ++c, ++g) {
+        const int sx = g % kTcNX, sa = g & 1;
+        if (!(ok = mbar_wait(x_full(sx), (uint32_t)(g / kTcNX) & 1u))) break;
+        if (g >= 2 && !(ok = mbar_wait(a_empty(sa), (uint32_t)((g >> 1) - 1) & 1u))) break;
+        const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage);
+        uint8_t* arow = A + sa * kTcAStage + (t0 >> 3) * 1024 + (t0 & 7) * 16;
+#pragma unroll 4
+        for (int jp = 0; jp < 8; ++jp) {
+          uint32_t d[4];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int j = 2 * jp + u, i = 16 * c + j;
+            uint32_t y = 0;
+            if (i < r) {
+              const uint4 k = CONST[i];
+              y = shoup_mul(xs[j * kTcRows + t0], k.y, k.z, k.x);
+              fs = fmaf(__uint2float_rn(y), __uint_as_float(k.w), fs);
+            } else if (i == r) {
+              y = (uint32_t)__float2int_rn(fs);  // kappa: every y_i of the tile is in fs by now
+            }
+            y_digits(y, d[2 * u], d[2 * u + 1]);
+          }
+          *reinterpret_cast<uint4*>(arow + jp * 128) = make_uint4(d[0], d[1], d[2], d[3]);
+        }
+        mbar_arrive(x_empty(sx));
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(a_full(sa));
+      }
     }
   } else {
-    // rows: coefficient n0 + tid
-    const int t = tid;
-    float fs = 0.f;
+    // E: warps 4-7 read TMEM lanes 32 (warp % 4) .. + 31, i.e. coefficient e = tid - 128
+    const int e = tid - kTcRows;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    int tl = 0;
     bool ok = true;
-    for (int c = 0; c < nch && ok; ++c) {
-      const int sx = c % kTcNX, sa = c & 1;
-      ok = mbar_wait(x_full(sx), (uint32_t)(c / kTcNX) & 1u);
-      if (ok && c >= 2) ok = mbar_wait(a_empty(sa), (uint32_t)((c >> 1) - 1) & 1u);
+    for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
+      int n0, poly, b;
+      tile_of(t, n0, poly, b);
+      const int ab = tl % sh.nacc;
+      ok = ok && mbar_wait(acc_full(ab), (uint32_t)(tl / sh.nacc) & 1u);
+      ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
       if (!ok) break;
-      const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage);
-      uint8_t* arow = A + sa * kTcAStage + (t >> 3) * 1024 + (t & 7) * 16;
-#pragma unroll 2
-      for (int jp = 0; jp < 8; ++jp) {
-        uint32_t d[4];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int j = 2 * jp + u, i = 16 * c + j;
-          uint32_t y = 0;
-          if (i < r) {
-            const uint2 ci = __ldg(cinv + i);
-            y = shoup_mul(xs[j * kTcRows + t], ci.x, ci.y, __ldg(qtab + i));
-            fs = fmaf(__uint2float_rn(y), __ldg(invq + i), fs);
-          } else if (i == r) {
-            y = (uint32_t)__float2int_rn(fs);  // kappa: every y_i is in fs by now
-          }
-          y_digits(y, d[2 * u], d[2 * u + 1]);
-        }
-        *reinterpret_cast<uint4*>(arow + jp * 128) = make_uint4(d[0], d[1], d[2], d[3]);
-      }
-      mbar_arrive(x_empty(sx));
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_arrive(a_full(sa));
-    }
-    if (ok) ok = mbar_wait(acc_full, 0);
-    ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld below is warp-collective
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // column sums -> limbs (limb column over the dead A/B stages), then the epilogue
-    uint32_t* col = reinterpret_cast<uint32_t*>(A);
-    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = tmem + lane_off + (uint32_t)(ab * sh.acc_cols);
       long long carry = 0;
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
       for (int m = 0; m < MT; ++m) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(lane_base + 16u * (uint32_t)m));
+            : "r"(base + 16u * (uint32_t)m));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -584,30 +640,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 1])) * 256LL +
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 2])) * 65536LL +
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 3])) * 16777216LL;
-          col[(size_t)(4 * m + q) * kTcRows + t] = (uint32_t)val;
+          LIMB[(size_t)(4 * m + q) * kTcRows + e] = (uint32_t)val;
           carry = val >> 32;
         }
       }
-      if (stage_add) ok = mbar_wait(add_full, 0);
-      if (ok)
-        crt_epilogue(col, t, kTcRows, 4 * MT, epi, poly, b, n0 + t, N, out, out_pstride, out_bstride,
-                     stage_add ? reinterpret_cast<const uint32_t*>(ADD) + t : nullptr, kTcRows);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(acc_empty(ab));
+      const uint32_t* add_s = nullptr;
+      if (sh.nadd) {
+        const int s = tl % sh.nadd;
+        if (!(ok = mbar_wait(add_full(s), (uint32_t)(tl / sh.nadd) & 1u))) break;
+        add_s = reinterpret_cast<const uint32_t*>(ADD + (size_t)s * add_limbs * 512) + e;
+      }
+      crt_epilogue(LIMB, e, kTcRows, 4 * MT, epi, poly, b, n0 + e, N, out, out_pstride, out_bstride, add_s, kTcRows);
+      if (sh.nadd) mbar_arrive(add_empty(tl % sh.nadd));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(sh.acc_cols * sh.nacc)
+                 : "memory");
   }
 }
 
-// Shared memory of k_crt_tc: header, residue stages, two A stages, two B
-// stages of P x 64 f16, and the staged addend limbs.
-static size_t tc_smem_bytes(int MT, int add_rows) {
-  return (size_t)kTcHead + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage + 2 * (size_t)MT * 16 * 128 +
-         (size_t)add_rows * 512;
+// Shared memory of k_crt_tc: header, prime constants, residue stages, two A
+// stages, two B stages of P x 64 f16, the epilogue's limb column and the
+// staged addend buffers.
+static size_t tc_smem_bytes(int MT, int add_limbs, int nadd) {
+  return (size_t)kTcHead + kTcConst + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage +
+         2 * (size_t)MT * 16 * 128 + (size_t)MT * 4 * kTcRows * 4 + (size_t)nadd * add_limbs * 512;
 }
 
 // Runs the tensor-core form when it applies; returns 1 if launched, 0 if the
@@ -616,29 +680,41 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
                      uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, int need, cudaStream_t st) {
   const int N = ctx->N;
   const int MT = (need + 3) / 4;
-  if (!ctx->d_crt_tc || r + 1 > 255 || N % kTcRows != 0 || MT > ctx->crt_tc_mt || (ip & 3) || (ib & 3) ||
-      ((uintptr_t)in & 15))
+  if (!ctx->d_crt_tc || r + 1 > 255 || r > kTcConst / 16 || N % kTcRows != 0 || MT > ctx->crt_tc_mt || (ip & 3) ||
+      (ib & 3) || ((uintptr_t)in & 15))
     return 0;
-  int stage_add = 0;
-  if (epi.add && epi.add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
-      !(epi.add_bstride & 3))
-    stage_add = 1;
-  if (epi.add && !stage_add) return 0;
-  const size_t smem = tc_smem_bytes(MT, stage_add ? epi.add_limbs : 0);
+  TcShape sh;
+  sh.r = r;
+  sh.MT = MT;
+  sh.nblk = N / kTcRows;
+  sh.npoly = npoly;
+  sh.ntiles = sh.nblk * npoly * nbatch;
+  sh.acc_cols = 32;
+  while (sh.acc_cols < 16 * MT) sh.acc_cols <<= 1;
+  sh.nacc = 2 * sh.acc_cols <= 512 ? 2 : 1;
+  const int add_limbs = epi.add ? epi.add_limbs : 0;
+  const bool stageable = add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
+                         !(epi.add_bstride & 3) && !(N & 3);
+  sh.nadd = 0;
+  if (stageable) {
+    if (tc_smem_bytes(MT, add_limbs, 2) <= 227 * 1024)
+      sh.nadd = 2;
+    else if (tc_smem_bytes(MT, add_limbs, 1) <= 227 * 1024)
+      sh.nadd = 1;
+  }
+  const size_t smem = tc_smem_bytes(MT, add_limbs, sh.nadd);
   if (smem > 227 * 1024) return 0;
-  int cols = 32;
-  while (cols < 16 * MT) cols <<= 1;
-  static thread_local int configured_dev = -1;
+  static thread_local int configured_dev = -1, nsm = 0;
   if (configured_dev != ctx->device) {
     cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     configured_dev = ctx->device;
   }
-  dim3 grid(N / kTcRows, npoly * nbatch);
+  const int grid = sh.ntiles < nsm ? sh.ntiles : nsm;
   ProfScope ps(ctx, FHE_K_CRT, 1, st);
   const size_t off = (size_t)r * (r - 1) / 2;
-  k_crt_tc<<<grid, kTcThreads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q, ctx->d_crt_inv + off,
-                                           ctx->d_invq, ctx->d_crt_tc + ctx->crt_tc_off[r], 16 * ctx->crt_tc_mt, MT,
-                                           cols, stage_add);
+  k_crt_tc<<<grid, kTcThreads, smem, st>>>(in, ip, ib, sh, out, op, ob, epi, N, ctx->d_q, ctx->d_crt_inv + off,
+                                           ctx->d_invq, ctx->d_crt_tc + ctx->crt_tc_off[r], 16 * ctx->crt_tc_mt);
   return 1;
 }
 

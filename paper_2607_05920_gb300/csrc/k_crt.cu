@@ -351,18 +351,23 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
 //              residues, as f16 digits into an A stage;
 //   warps 4-7  (E) per tile: S_p from the thread's own TMEM lane, carried into
 //              32-bit limbs, the accumulator released, then the epilogue;
-//   warp 8     bulk copies (TMA engine): residue rows, B chunks, the addend;
-//   warp 9     TMEM allocation and the MMA issue (one thread).
+//   warps 16, 18  bulk copies (TMA engine): residue rows and the addend; B slices;
+//   warp 17    TMEM allocation and the MMA issue (one thread).
 // With P <= 256 two accumulators alternate, so the epilogue of one tile runs
 // under the GEMM of the next.  K runs in chunks of 64 (16 primes).  Every
 // wait is bounded and reports a timeout through fhe_sync.
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 320;
+constexpr int kTcYWarps = 8;                // two threads per coefficient row
+constexpr int kTcEWarps = 8;                // two groups of four, alternating tiles
+constexpr int kTcWarpProd = kTcYWarps + kTcEWarps;  // residues and addends
+constexpr int kTcWarpMma = kTcWarpProd + 1;         // TMEM owner, MMA issue
+constexpr int kTcWarpProdB = kTcWarpMma + 1;        // B slices
+constexpr int kTcThreads = 32 * (kTcWarpProdB + 1);
 constexpr int kTcNX = 3;                    // residue stages
 constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficients
 constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
 constexpr int kTcHead = 1024;               // mbarriers + TMEM address
-constexpr int kTcConst = 4096;              // per prime {q, cinv, cinv shoup, 1/q}
+constexpr int kTcFsx = 2048;                // quotient partial sums, [tile parity][half][row]
 
 __device__ unsigned int g_fhe_dev_status = 0;
 
@@ -377,15 +382,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Waits for the phase of the given parity to complete; gives up after a
-// bounded number of polls, records the timeout and returns false.
+// Waits for the phase of the given parity to complete.  Each try_wait
+// suspends the thread (up to the hint, 0.5 ms) until the phase completes, so
+// waiting warps take no issue slots; after a bounded number of tries (about
+// 2 s) the wait gives up, records the timeout and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 24); ++it) {
+  for (int it = 0; it < 4096; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(500000u)
         : "memory");
     if (ok) return true;
   }
@@ -408,8 +415,7 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db,
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accum)
-      : "memory");
+      "l"(da), "l"(db), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
@@ -427,11 +433,90 @@ __device__ __forceinline__ void y_digits(uint32_t y, uint32_t& lo, uint32_t& hi)
   asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(hi) : "r"(h), "r"(0x64006480u));
 }
 
+// Streaming forms of the two hot epilogues, fed limb by limb (low to high)
+// straight from the carry of the column sums, so no limb column is stored.
+// They compute exactly what crt_epilogue computes for these kinds:
+//  kStore: X mod 2^ob;
+//  kRelin: Y = ((X + 2^(s-1)) >> s) + A mod 2^ob, then, if k2 > 0,
+//          (Y + 2^(k2-1)) >> k2 mod 2^(ob-k2).
+// (X + 2^(s-1)) >> s = (X >> s) + bit_{s-1}(X): the rounding bit sits in a
+// limb that arrives before the first shifted limb, and every later stage only
+// needs the limb after the current one, so each arriving limb moves every
+// stage by at most one limb.
+struct RelinStream {
+  // configuration
+  int sl, sb, rl, rbit;  // relin shift s in limbs / bits, limb and bit of bit s-1
+  int nz;                // limbs of the mod-2^ob value
+  uint32_t zmask;        // mask of its top limb
+  const uint32_t* add;   // addend limbs (stride add_stride), or null
+  int add_limbs, add_stride;
+  int k2, kl, kb, rl2, rbit2, nf;  // rescale shift, limbs of the mod-2^(ob-k2) value
+  uint32_t wmask;
+  int out_limbs;
+  uint32_t* dst;
+  int N;
+  // state
+  uint32_t xprev = 0, cA = 0, cB = 0, zprev = 0, cC = 0;
+  int j = 0, zi = 0, i = 0;
+
+  __device__ __forceinline__ void store(uint32_t w) {
+    if (i < out_limbs) dst[(size_t)i * N] = w;
+    ++i;
+  }
+  __device__ __forceinline__ void push_z(uint32_t z) {
+    if (k2 == 0) {
+      if (zi < nz) store(z);
+      ++zi;
+      return;
+    }
+    if (zi == rl2) cC = (z >> rbit2) & 1u;
+    if (zi >= kl + 1 && i < nf) {
+      uint32_t w = __funnelshift_r(zprev, z, kb) + cC;
+      cC = (w < cC) ? 1u : 0u;
+      if (i == nf - 1) w &= wmask;
+      store(w);
+    }
+    zprev = z;
+    ++zi;
+  }
+  __device__ __forceinline__ void push_x(int l, uint32_t x) {
+    if (l == rl) cA = (x >> rbit) & 1u;
+    if (l >= sl + 1 && j < nz) {
+      uint32_t y = __funnelshift_r(xprev, x, sb) + cA;
+      cA = (y < cA) ? 1u : 0u;
+      const uint32_t a = (add && j < add_limbs) ? add[(size_t)j * add_stride] : 0u;
+      const uint64_t zz = (uint64_t)y + a + cB;
+      cB = (uint32_t)(zz >> 32);
+      uint32_t z = (uint32_t)zz;
+      if (j == nz - 1) z &= zmask;
+      ++j;
+      push_z(z);
+    }
+    xprev = x;
+  }
+  // after the last limb: the stages drain on zero limbs, then the store is padded
+  __device__ __forceinline__ void finish(int l) {
+    while (j < nz) push_x(l++, 0u);
+    if (k2 > 0)
+      while (i < nf) push_z(0u);
+    while (i < out_limbs) store(0u);
+  }
+};
+
 struct TcShape {
   int r, MT, nblk, npoly, ntiles;  // primes, output m-tiles, 128-blocks per polynomial, tiles
   int acc_cols, nacc;              // TMEM columns per accumulator, accumulators
   int nadd;                        // staged addend buffers (0: the epilogue reads the addend from global)
+  int const_bytes;                 // shared bytes of the per-prime constants
 };
+
+// Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
+// residue stages, two A stages (K 64), two B slices (K 32), one limb column
+// per epilogue group and the staged addend buffers.
+static size_t tc_smem_bytes(const TcShape& sh, int add_limbs) {
+  return (size_t)kTcHead + sh.const_bytes + kTcFsx + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage +
+         2 * (size_t)sh.MT * 16 * 64 + 2 * (size_t)sh.MT * 4 * kTcRows * 4 + (size_t)sh.nadd * add_limbs * 512;
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_crt_tc(const uint32_t* __restrict__ in, size_t in_pstride, size_t in_bstride, TcShape sh,
@@ -442,16 +527,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = sh.r, MT = sh.MT;
   const int P = 16 * MT;
-  const int KS = (r + 4) >> 2;  // k-steps of 16 over the 4 (r + 1) digits
+  const int KS = (r + 4) >> 2;    // k-steps of 16 over the 4 (r + 1) digits
   const int nch = (KS + 3) >> 2;  // chunks of 4 k-steps (16 primes)
-  const uint32_t bstage = (uint32_t)P * 128u;
+  const uint32_t bslice = (uint32_t)P * 64u;  // bytes of a K-32 slice of B
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   uint4* CONST = reinterpret_cast<uint4*>(smem + kTcHead);
-  uint8_t* X = smem + kTcHead + kTcConst;
+  float* FSX = reinterpret_cast<float*>(smem + kTcHead + sh.const_bytes);
+  uint8_t* X = smem + kTcHead + sh.const_bytes + kTcFsx;
   uint8_t* A = X + kTcNX * kTcXStage;
   uint8_t* B = A + 2 * kTcAStage;
-  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + 2 * bstage);
-  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (size_t)4 * MT * kTcRows);
+  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + 2 * bslice);
+  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (size_t)2 * 4 * MT * kTcRows);
   const uint32_t bar0 = smem_addr(smem);
   auto x_full = [&](int s) { return bar0 + 8u * s; };
   auto x_empty = [&](int s) { return bar0 + 8u * (3 + s); };
@@ -459,10 +545,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto a_empty = [&](int s) { return bar0 + 8u * (8 + s); };
   auto b_full = [&](int s) { return bar0 + 8u * (10 + s); };
   auto b_empty = [&](int s) { return bar0 + 8u * (12 + s); };
+  // per tile parity (= epilogue group): each completes once every two tiles
   auto acc_full = [&](int s) { return bar0 + 8u * (14 + s); };
   auto acc_empty = [&](int s) { return bar0 + 8u * (16 + s); };
   auto add_full = [&](int s) { return bar0 + 8u * (18 + s); };
   auto add_empty = [&](int s) { return bar0 + 8u * (20 + s); };
+  auto fsx_bar = [&](int s) { return bar0 + 8u * (22 + s); };  // per tile parity: Y partial sums written
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 512);
   auto tile_of = [&](int t, int& n0, int& poly, int& b) {
     const int py = t / sh.nblk;
@@ -474,10 +562,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < kTcNX; ++s) {
       mbar_init(x_full(s), 1);
-      mbar_init(x_empty(s), kTcRows);
+      mbar_init(x_empty(s), 32 * kTcYWarps);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(a_full(s), kTcRows);
+      mbar_init(a_full(s), 32 * kTcYWarps);
       mbar_init(a_empty(s), 1);
       mbar_init(b_full(s), 1);
       mbar_init(b_empty(s), 1);
@@ -485,6 +573,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(acc_empty(s), kTcRows);
       mbar_init(add_full(s), 1);
       mbar_init(add_empty(s), kTcRows);
+      mbar_init(fsx_bar(s), 32 * kTcYWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -492,7 +581,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint2 ci = __ldg(cinv + i);
     CONST[i] = make_uint4(__ldg(qtab + i), ci.x, ci.y, __float_as_uint(__ldg(invq + i)));
   }
-  if (warp == 9) {
+  if (warp == kTcWarpMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
                  "r"(sh.acc_cols * sh.nacc)
                  : "memory");
@@ -503,9 +592,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 8) {
+  if (warp == kTcWarpProd) {
     if (lane == 0) {
-      // producer: per tile the addend limbs, per chunk the residue rows and the B chunk
+      // producer: per tile the addend limbs, per chunk the residue rows and two B slices
       int g = 0, tl = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
@@ -513,96 +602,144 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tile_of(t, n0, poly, b);
         if (sh.nadd) {
           const int s = tl % sh.nadd;
-          if (tl >= sh.nadd) ok = mbar_wait(add_empty(s), (uint32_t)((tl / sh.nadd) - 1) & 1u);
-          if (!ok) break;
+          if (tl >= sh.nadd &&
+              !(ok = mbar_wait(add_empty((tl - sh.nadd) & 1), (uint32_t)((tl - sh.nadd) >> 1) & 1u)))
+            break;
           const bool has = add_limbs > 0 && poly < epi.add_polys;
-          mbar_expect_tx(add_full(s), has ? (uint32_t)add_limbs * 512u : 0u);
+          mbar_expect_tx(add_full(tl & 1), has ? (uint32_t)add_limbs * 512u : 0u);
           if (has) {
             const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0;
             uint8_t* dst = ADD + (size_t)s * add_limbs * 512;
             for (int l = 0; l < add_limbs; ++l)
-              bulk_g2s(smem_addr(dst + 512 * l), ad + (size_t)l * N, 512u, add_full(s));
+              bulk_g2s(smem_addr(dst + 512 * l), ad + (size_t)l * N, 512u, add_full(tl & 1));
           }
         }
         const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n0;
-        for (int c = 0; c < nch; ++c, ++g) {
+        for (int c = 0; c < nch && ok; ++c, ++g) {
           const int sx = g % kTcNX;
           if (g >= kTcNX && !(ok = mbar_wait(x_empty(sx), (uint32_t)((g / kTcNX) - 1) & 1u))) break;
           const int rows = max(0, min(16, r - 16 * c));
           mbar_expect_tx(x_full(sx), (uint32_t)rows * 512u);
           for (int j = 0; j < rows; ++j)
             bulk_g2s(smem_addr(X + sx * kTcXStage + 512 * j), src + (size_t)(16 * c + j) * N, 512u, x_full(sx));
-          const int sb = g & 1;
-          if (g >= 2 && !(ok = mbar_wait(b_empty(sb), (uint32_t)((g >> 1) - 1) & 1u))) break;
-          mbar_expect_tx(b_full(sb), bstage);
-          bulk_g2s(smem_addr(B + sb * bstage), bmat + (size_t)c * pmax * 64, bstage, b_full(sb));
         }
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == kTcWarpProdB) {
     if (lane == 0) {
-      // MMA issue: D[128][P] += A_chunk B_chunk^T, output columns in pieces of at most 256
-      const int nsplit = (MT + 15) / 16;
+      // B slices (K 32 each, two per chunk), the same sequence for every tile
+      int gb = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x)
+        for (int c2 = 0; c2 < 2 * nch; ++c2, ++gb) {
+          const int sb = gb & 1;
+          if (gb >= 2 && !(ok = mbar_wait(b_empty(sb), (uint32_t)((gb >> 1) - 1) & 1u))) break;
+          mbar_expect_tx(b_full(sb), bslice);
+          bulk_g2s(smem_addr(B + sb * bslice), bmat + (size_t)c2 * pmax * 32, bslice, b_full(sb));
+        }
+    }
+  } else if (warp == kTcWarpMma) {
+    if (lane == 0) {
+      // MMA issue: D[128][P] += A_chunk B_slice^T, output columns in pieces of at most 256.
+      // This one thread's instruction latency bounds the MMA rate: everything per
+      // split is precomputed, descriptors advance by adding to the address field.
+      const int nsplit = (MT + 15) / 16;  // 1 or 2 (P <= 512)
+      const int mh = nsplit > 1 ? MT / 2 : MT;  // m-tiles of the first piece
+      const uint32_t col1 = 16u * (uint32_t)mh;
+      const uint64_t boff1 = (uint64_t)((2u * (uint32_t)mh * 512u) >> 4);
+      const uint32_t idesc0 = (1u << 4) | ((16u * (uint32_t)mh >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+      const uint32_t idesc1 = (1u << 4) | ((16u * (uint32_t)(MT - mh) >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+      const uint64_t adesc0 = tc_desc(smem_addr(A), 128u, 1024u);
+      const uint64_t bdesc0 = tc_desc(smem_addr(B), 128u, 512u);
       int g = 0, tl = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
         const int ab = tl % sh.nacc;
-        if (tl >= sh.nacc && !(ok = mbar_wait(acc_empty(ab), (uint32_t)((tl / sh.nacc) - 1) & 1u))) break;
+        if (tl >= sh.nacc &&
+            !(ok = mbar_wait(acc_empty((tl - sh.nacc) & 1), (uint32_t)((tl - sh.nacc) >> 1) & 1u)))
+          break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(ab * sh.acc_cols);
-        for (int c = 0; c < nch; ++c, ++g) {
+        for (int c = 0; c < nch && ok; ++c, ++g) {
           const int s = g & 1;
-          const uint32_t par = (uint32_t)(g >> 1) & 1u;
-          if (!(ok = mbar_wait(a_full(s), par)) || !(ok = mbar_wait(b_full(s), par))) break;
-          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t abase = smem_addr(A + s * kTcAStage), bbase = smem_addr(B + s * bstage);
+          if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
+          const uint64_t adesc = adesc0 + (uint64_t)((s * kTcAStage) >> 4);
           const int nks = min(4, KS - 4 * c);
-          for (int ks = 0; ks < nks; ++ks) {
-            for (int sp = 0; sp < nsplit; ++sp) {
-              const int m0 = sp * MT / nsplit, m1 = (sp + 1) * MT / nsplit;
-              const uint32_t n = 16u * (uint32_t)(m1 - m0);
-              const uint32_t idesc = (1u << 4) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-              const uint64_t da = tc_desc(abase + 256u * ks, 128u, 1024u);
-              const uint64_t db = tc_desc(bbase + (uint32_t)(2 * m0) * 1024u + 256u * ks, 128u, 1024u);
-              tc_mma(dbase + 16u * (uint32_t)m0, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          for (int h = 0; h < 2; ++h) {
+            const int gb = 2 * g + h, sb = gb & 1;
+            if (!(ok = mbar_wait(b_full(sb), (uint32_t)(gb >> 1) & 1u))) break;
+            const uint64_t bdesc = bdesc0 + (uint64_t)((sb * bslice) >> 4);
+            const int ke = min(nks, 2 * h + 2);
+            for (int ks = 2 * h; ks < ke; ++ks) {
+              const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+              const uint64_t da = adesc + (uint64_t)(16 * ks);            // + 256 B per k-step
+              const uint64_t db = bdesc + (uint64_t)(16 * (ks & 1));      // + 256 B per k-step
+              tc_mma(dbase, da, db, idesc0, accum);
+              if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
             }
+            tc_commit(b_empty(sb));
           }
           tc_commit(a_empty(s));
-          tc_commit(b_empty(s));
         }
         if (!ok) break;
-        tc_commit(acc_full(ab));
+        tc_commit(acc_full(tl & 1));
       }
     }
-  } else if (warp < 4) {
-    // Y: digits of y_i (and kappa) for coefficient n0 + tid of every tile
-    const int t0 = tid;
-    int g = 0;
+  } else if (warp < kTcYWarps) {
+    // Y: digits of y_i (and kappa); thread (t, h) handles primes 8h .. 8h + 7 of every chunk of row t
+    const int t0 = tid & (kTcRows - 1), h = tid >> 7;
+    int g = 0, tly = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x) {
+    for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tly) {
       float fs = 0.f;
       for (int c = 0; c < nch; ++c, ++g) {
         const int sx = g % kTcNX, sa = g & 1;
         if (!(ok = mbar_wait(x_full(sx), (uint32_t)(g / kTcNX) & 1u))) break;
         if (g >= 2 && !(ok = mbar_wait(a_empty(sa), (uint32_t)((g >> 1) - 1) & 1u))) break;
-        const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage);
-        uint8_t* arow = A + sa * kTcAStage + (t0 >> 3) * 1024 + (t0 & 7) * 16;
-#pragma unroll 4
-        for (int jp = 0; jp < 8; ++jp) {
-          uint32_t d[4];
+        const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage) + 8 * h * kTcRows + t0;
+        uint8_t* arow = A + sa * kTcAStage + (t0 >> 3) * 1024 + (t0 & 7) * 16 + 4 * h * 128;
+        const int i0 = 16 * c + 8 * h;
+        uint32_t yv[8];
+        if (16 * c + 16 <= r) {
+          // eight real primes: every load first, then the arithmetic
+          uint32_t xv[8];
+          uint4 kq[8];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int j = 2 * jp + u, i = 16 * c + j;
-            uint32_t y = 0;
+          for (int j = 0; j < 8; ++j) xv[j] = xs[j * kTcRows];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) kq[j] = CONST[i0 + j];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) yv[j] = shoup_mul(xv[j], kq[j].y, kq[j].z, kq[j].x);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) fs = fmaf(__uint2float_rn(yv[j]), __uint_as_float(kq[j].w), fs);
+        } else {
+          // the chunk holding kappa (i = r): both halves exchange their partial quotient sums
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j;
+            yv[j] = 0u;
             if (i < r) {
               const uint4 k = CONST[i];
-              y = shoup_mul(xs[j * kTcRows + t0], k.y, k.z, k.x);
-              fs = fmaf(__uint2float_rn(y), __uint_as_float(k.w), fs);
-            } else if (i == r) {
-              y = (uint32_t)__float2int_rn(fs);  // kappa: every y_i of the tile is in fs by now
+              yv[j] = shoup_mul(xs[j * kTcRows], k.y, k.z, k.x);
+              fs = fmaf(__uint2float_rn(yv[j]), __uint_as_float(k.w), fs);
             }
-            y_digits(y, d[2 * u], d[2 * u + 1]);
           }
+          float* fx = FSX + (tly & 1) * 2 * kTcRows;
+          fx[h * kTcRows + t0] = fs;
+          mbar_arrive(fsx_bar(tly & 1));
+          if (!(ok = mbar_wait(fsx_bar(tly & 1), (uint32_t)(tly >> 1) & 1u))) break;
+          if (r >= i0 && r < i0 + 8) {
+            const uint32_t kappa = (uint32_t)__float2int_rn(fx[t0] + fx[kTcRows + t0]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (i0 + j == r) yv[j] = kappa;
+          }
+        }
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+          uint32_t d[4];
+          y_digits(yv[2 * jp], d[0], d[1]);
+          y_digits(yv[2 * jp + 1], d[2], d[3]);
           *reinterpret_cast<uint4*>(arow + jp * 128) = make_uint4(d[0], d[1], d[2], d[3]);
         }
         mbar_arrive(x_empty(sx));
@@ -611,20 +748,67 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // E: warps 4-7 read TMEM lanes 32 (warp % 4) .. + 31, i.e. coefficient e = tid - 128
-    const int e = tid - kTcRows;
+    // E: two groups of four warps take alternate tiles; warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int e = tid - 32 * kTcYWarps;
+    const int eg = e >> 7, ec = e & (kTcRows - 1);
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    uint32_t* limb = LIMB + (size_t)eg * 4 * MT * kTcRows + ec;
     int tl = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
+      if ((tl & 1) != eg) continue;
       int n0, poly, b;
       tile_of(t, n0, poly, b);
       const int ab = tl % sh.nacc;
-      ok = ok && mbar_wait(acc_full(ab), (uint32_t)(tl / sh.nacc) & 1u);
+      ok = ok && mbar_wait(acc_full(eg), (uint32_t)(tl >> 1) & 1u);
       ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tmem + lane_off + (uint32_t)(ab * sh.acc_cols);
+      const int ob = epi.item_bits ? __ldg(epi.item_bits + b) : epi.out_bits;
+      const bool has_add = epi.add && poly < epi.add_polys;
+      const int32_t* smallp = poly == 0 ? epi.small : (poly == 1 ? epi.small1 : nullptr);
+      // 0: limb column + crt_epilogue, 1: masked store, 2: relinearisation stream
+      const int mode = (epi.kind == Epi::kStore && !has_add && !smallp) ? 1
+                       : (epi.kind == Epi::kRelin && epi.shift > 0 && !smallp) ? 2 : 0;
+      // with two accumulators the stream runs off TMEM directly; with one the
+      // accumulator is drained into the limb column first and released
+      const bool direct = sh.nacc == 2 && mode != 0;
+      const uint32_t* add_s =
+          sh.nadd ? reinterpret_cast<const uint32_t*>(ADD + (size_t)(tl % sh.nadd) * add_limbs * 512) + ec : nullptr;
+      uint32_t* dst = out + (size_t)b * out_bstride + (size_t)poly * out_pstride + n0 + ec;
+      const int nlo = (ob + 31) >> 5;
+      RelinStream rs;
+      if (mode == 2) {
+        const int sft = epi.shift;
+        rs.sl = sft >> 5;
+        rs.sb = sft & 31;
+        rs.rl = (sft - 1) >> 5;
+        rs.rbit = (sft - 1) & 31;
+        rs.nz = nlo;
+        rs.zmask = limb_mask(nlo - 1, ob);
+        rs.add = has_add ? (add_s ? add_s
+                                  : epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0 + ec)
+                         : nullptr;
+        rs.add_limbs = epi.add_limbs;
+        rs.add_stride = add_s ? kTcRows : N;
+        rs.k2 = epi.k2;
+        rs.kl = epi.k2 >> 5;
+        rs.kb = epi.k2 & 31;
+        rs.rl2 = epi.k2 > 0 ? (epi.k2 - 1) >> 5 : 0;
+        rs.rbit2 = epi.k2 > 0 ? (epi.k2 - 1) & 31 : 0;
+        const int fb = ob - epi.k2;
+        rs.nf = (fb + 31) >> 5;
+        rs.wmask = limb_mask(rs.nf - 1, fb);
+        rs.out_limbs = epi.out_limbs;
+        rs.dst = dst;
+        rs.N = N;
+      }
+      bool have_add_stage = false;
+      if (direct && mode == 2 && sh.nadd) {
+        if (!(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
+        have_add_stage = true;
+      }
       long long carry = 0;
       for (int m = 0; m < MT; ++m) {
         uint32_t v[16];
@@ -640,38 +824,57 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 1])) * 256LL +
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 2])) * 65536LL +
                                 (long long)__float2int_rn(__uint_as_float(v[4 * q + 3])) * 16777216LL;
-          LIMB[(size_t)(4 * m + q) * kTcRows + e] = (uint32_t)val;
           carry = val >> 32;
+          const int l = 4 * m + q;
+          const uint32_t x = (uint32_t)val;
+          if (!direct) {
+            limb[(size_t)l * kTcRows] = x;
+          } else if (mode == 1) {
+            if (l < epi.out_limbs) dst[(size_t)l * N] = l < nlo ? (x & limb_mask(l, ob)) : 0u;
+          } else {
+            rs.push_x(l, x);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      mbar_arrive(acc_empty(ab));
-      const uint32_t* add_s = nullptr;
-      if (sh.nadd) {
-        const int s = tl % sh.nadd;
-        if (!(ok = mbar_wait(add_full(s), (uint32_t)(tl / sh.nadd) & 1u))) break;
-        add_s = reinterpret_cast<const uint32_t*>(ADD + (size_t)s * add_limbs * 512) + e;
+      mbar_arrive(acc_empty(eg));
+      if (sh.nadd && !have_add_stage && !(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
+      if (direct) {
+        if (mode == 2) rs.finish(4 * MT);
+      } else if (mode == 1) {
+        for (int l0 = 0; l0 < epi.out_limbs; l0 += 8) {
+          uint32_t xv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xv[q] = (l0 + q < nlo) ? limb[(size_t)(l0 + q) * kTcRows] : 0u;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (l0 + q < epi.out_limbs) dst[(size_t)(l0 + q) * N] = xv[q] & limb_mask(l0 + q, ob);
+        }
+      } else if (mode == 2) {
+        for (int l0 = 0; l0 < 4 * MT; l0 += 8) {
+          uint32_t xv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xv[q] = (l0 + q < 4 * MT) ? limb[(size_t)(l0 + q) * kTcRows] : 0u;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (l0 + q < 4 * MT) rs.push_x(l0 + q, xv[q]);
+        }
+        rs.finish(4 * MT);
+      } else {
+        crt_epilogue(LIMB + (size_t)eg * 4 * MT * kTcRows, ec, kTcRows, 4 * MT, epi, poly, b, n0 + ec, N, out,
+                     out_pstride, out_bstride, add_s, kTcRows);
       }
-      crt_epilogue(LIMB, e, kTcRows, 4 * MT, epi, poly, b, n0 + e, N, out, out_pstride, out_bstride, add_s, kTcRows);
-      if (sh.nadd) mbar_arrive(add_empty(tl % sh.nadd));
+      if (sh.nadd) mbar_arrive(add_empty(eg));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 9) {
+  if (warp == kTcWarpMma) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(sh.acc_cols * sh.nacc)
                  : "memory");
   }
-}
-
-// Shared memory of k_crt_tc: header, prime constants, residue stages, two A
-// stages, two B stages of P x 64 f16, the epilogue's limb column and the
-// staged addend buffers.
-static size_t tc_smem_bytes(int MT, int add_limbs, int nadd) {
-  return (size_t)kTcHead + kTcConst + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage +
-         2 * (size_t)MT * 16 * 128 + (size_t)MT * 4 * kTcRows * 4 + (size_t)nadd * add_limbs * 512;
 }
 
 // Runs the tensor-core form when it applies; returns 1 if launched, 0 if the
@@ -680,8 +883,8 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
                      uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, int need, cudaStream_t st) {
   const int N = ctx->N;
   const int MT = (need + 3) / 4;
-  if (!ctx->d_crt_tc || r + 1 > 255 || r > kTcConst / 16 || N % kTcRows != 0 || MT > ctx->crt_tc_mt || (ip & 3) ||
-      (ib & 3) || ((uintptr_t)in & 15))
+  if (!ctx->d_crt_tc || r + 1 > 255 || N % kTcRows != 0 || MT > ctx->crt_tc_mt || (ip & 3) || (ib & 3) ||
+      ((uintptr_t)in & 15))
     return 0;
   TcShape sh;
   sh.r = r;
@@ -692,17 +895,18 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
   sh.acc_cols = 32;
   while (sh.acc_cols < 16 * MT) sh.acc_cols <<= 1;
   sh.nacc = 2 * sh.acc_cols <= 512 ? 2 : 1;
+  sh.const_bytes = (r * 16 + 1023) & ~1023;
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   const bool stageable = add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
                          !(epi.add_bstride & 3) && !(N & 3);
   sh.nadd = 0;
   if (stageable) {
-    if (tc_smem_bytes(MT, add_limbs, 2) <= 227 * 1024)
-      sh.nadd = 2;
-    else if (tc_smem_bytes(MT, add_limbs, 1) <= 227 * 1024)
-      sh.nadd = 1;
+    for (int na = 2; na >= 1 && !sh.nadd; --na) {
+      sh.nadd = na;
+      if (tc_smem_bytes(sh, add_limbs) > 227 * 1024) sh.nadd = 0;
+    }
   }
-  const size_t smem = tc_smem_bytes(MT, add_limbs, sh.nadd);
+  const size_t smem = tc_smem_bytes(sh, add_limbs);
   if (smem > 227 * 1024) return 0;
   static thread_local int configured_dev = -1, nsm = 0;
   if (configured_dev != ctx->device) {

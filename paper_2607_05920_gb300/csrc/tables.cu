@@ -213,7 +213,7 @@ static void balanced_bytes(const uint32_t* limbs, int8_t* out) {
 // byte column p of sum_i y_i C_i (C_i = M_r/q_i, C_r = -M_r with y_r = kappa)
 // is S_p = sum_i sum_a d_{i,a} c_{i,p-a}, d_{i,a} the balanced bytes of y_i,
 // c_{i,.} those of C_i: a GEMM with K = 4 i + a and the B operand
-// B[p][4 i + a] = c_{i,p-a}, stored per chunk of 64 k as K-major core
+// B[p][4 i + a] = c_{i,p-a}, stored per slice of 32 k as K-major core
 // matrices (8 rows x 8 f16) in the order [p/8][k/8][p%8][k%8].
 static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const std::vector<uint32_t>& negm) {
   const int R = ctx->R;
@@ -242,7 +242,8 @@ static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const s
         for (int k = 0; k < 64; ++k) {
           const int kg = 64 * c + k, i = kg >> 2, a = kg & 3, pa = p - a;
           if (i > r || pa < 0) continue;
-          base[(size_t)c * P * 64 + ((size_t)(p >> 3) * 8 + (k >> 3)) * 64 + (p & 7) * 8 + (k & 7)] =
+          const int kh = kg >> 5, kk = kg & 31;
+          base[(size_t)kh * P * 32 + ((size_t)(p >> 3) * 4 + (kk >> 3)) * 64 + (p & 7) * 8 + (kk & 7)] =
               h16[dig[(size_t)i * 4 * kMaxLimbs + pa] + 128];
         }
   }

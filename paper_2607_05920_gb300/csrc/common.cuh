@@ -108,6 +108,11 @@ struct fhe_ctx {
   // (B[p][4i + a] = c_{i,p-a}); K in chunks of 64, each chunk [p/8][k/8][p%8][k%8] (K-major core
   // matrices, no swizzle) for p < 16 crt_tc_mt; set r starts at crt_tc_off[r] (f16 elements)
   uint16_t* d_crt_tc = nullptr;
+  // tensor-core lift: B operand [4R rows (i, a)][4 kMaxLiftLimbs k] f16 in K-major core-matrix order
+  // [row/8][k/8][row%8][k%8], digit a of (2^(8k) 2^32 mod q_i) (digits 0..2 balanced, 3 in [0, 128]);
+  // and per L the folded offset + 2^17 q_i, [kMaxLiftLimbs + 1][R] (see k_lift_tc)
+  uint16_t* d_lift_tc = nullptr;
+  uint64_t* d_lift_off = nullptr;
   std::vector<size_t> crt_tc_off;
   int crt_tc_mt = 0;              // output byte columns covered, in 16s
   int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 1 Garner (Eq. garner_mrc),
@@ -243,7 +248,8 @@ struct EpiArgs {
 };
 // in: [nbatch][npoly][r][N] (poly stride in_pstride, batch in_bstride);
 // out: [nbatch][npoly][out_limbs][N] (strides out_pstride, out_bstride).
-unsigned int read_dev_status();  // nonzero (then cleared) after a bounded device wait gave up
+unsigned int read_dev_status();   // nonzero (then cleared) after a bounded device wait gave up
+unsigned int read_lift_status();  // the same for the lift kernels
 int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, size_t in_bstride, int r, int npoly,
                   int nbatch, uint32_t* out, size_t out_pstride, size_t out_bstride, const EpiArgs& epi,
                   cudaStream_t st);

@@ -20,6 +20,12 @@
 #include "common.cuh"
 
 namespace fhe {
+__device__ unsigned int g_fhe_dev_status = 0;  // set when a bounded device wait gives up
+}
+#define FHE_TC_STATUS fhe::g_fhe_dev_status
+#include "tc.cuh"
+
+namespace fhe {
 
 constexpr int kCrtThreads = 128;
 
@@ -368,58 +374,6 @@ constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficien
 constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
 constexpr int kTcHead = 1024;               // mbarriers + TMEM address
 constexpr int kTcFsx = 2048;                // quotient partial sums, [tile parity][half][row]
-
-__device__ unsigned int g_fhe_dev_status = 0;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-// Waits for the phase of the given parity to complete.  Each try_wait
-// suspends the thread (up to the hint, 0.5 ms) until the phase completes, so
-// waiting warps take no issue slots; after a bounded number of tries (about
-// 2 s) the wait gives up, records the timeout and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < 4096; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(500000u)
-        : "memory");
-    if (ok) return true;
-  }
-  atomicOr(&g_fhe_dev_status, 1u);
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
-// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
-// byte step between 8-row groups.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
-}
 
 // Balanced bytes of y < 2^31 as two f16x2 registers {d0, d1}, {d2, d3}:
 // e = y + 0x808080, d_a = byte_a(e) - 128 for a < 3, d_3 = byte_3(e) <= 128.
@@ -925,9 +879,9 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
 // Device status word: nonzero after a bounded wait gave up.  Read and cleared.
 unsigned int read_dev_status() {
   unsigned int v = 0, z = 0;
-  if (cudaMemcpyFromSymbol(&v, g_fhe_dev_status, sizeof(v)) != cudaSuccess) return 0;
+  if (cudaMemcpyFromSymbol(&v, g_fhe_dev_status, sizeof(v)) != cudaSuccess) v = 0;
   if (v) cudaMemcpyToSymbol(g_fhe_dev_status, &z, sizeof(z));
-  return v;
+  return v | read_lift_status();
 }
 
 template <int LB>

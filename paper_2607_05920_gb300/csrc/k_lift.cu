@@ -11,6 +11,12 @@
 #include "common.cuh"
 
 namespace fhe {
+__device__ unsigned int g_lift_dev_status = 0;  // set when a bounded device wait gives up
+}
+#define FHE_TC_STATUS fhe::g_lift_dev_status
+#include "tc.cuh"
+
+namespace fhe {
 
 constexpr int kLiftThreads = 128;
 
@@ -145,6 +151,276 @@ __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint
   }
 }
 
+// ------------------------------------------------------ lift, tensor cores
+// The lift is a dense contraction too: with the limbs' bytes b_k and
+// d_k = b_k - 128 in [-128, 127], and C_{i,k} = 2^(8k) 2^32 mod q_i split into
+// digits c_{i,k,a} (|c| <= 128),
+//   T_i = sum_a 256^a S_{i,a},  S_{i,a} = sum_k d_k c_{i,k,a},
+// is congruent to (x - 128 sum_k 256^k) 2^32 mod q_i.  S = A B^T with A the
+// digits of the 128 coefficients of a tile ([128][K = 4L]) and B the
+// constants ([4r][K]); |S| <= 4L 2^14 < 2^22 for L < 64, exact in fp32 and
+// converted to integers by the 1.5 2^23 magic-number addition.  Adding the
+// folded offset (and 2^17 q_i) and one Montgomery reduction gives x mod q_i.
+// The constants stay resident in shared memory for the whole (persistent)
+// kernel; the output columns are split into two TMEM accumulators (residue
+// halves) so each half's drain overlaps the other half's MMAs.  Warp roles:
+//   warps 0-7   limbs -> digit tile A (two threads per coefficient row),
+//               the next tile's limbs loaded while the MMAs read A;
+//   warps 8-23  four epilogue groups, two per half, alternating 4-residue
+//               column blocks: TMEM -> integers -> Montgomery -> residue rows;
+//   warp 24     TMEM allocation and the MMA issue (one thread).
+constexpr int kLtRows = 128;
+constexpr int kLtYWarps = 8, kLtEWarps = 16;
+constexpr int kLtWarpMma = kLtYWarps + kLtEWarps;
+constexpr int kLtThreads = 32 * (kLtWarpMma + 1);
+
+struct LtShape {
+  int r, L, Kpad;          // primes, limbs, K padded to 16
+  int r0, n0, n1;          // residues of the first half; MMA N of each half (n1 = 0: one half)
+  int acc_cols;            // TMEM columns per accumulator
+  int nblk, npoly, ntiles;
+};
+
+static size_t lt_smem_bytes(const LtShape& sh) {
+  return 512 + 16 * 128 + (size_t)(sh.n0 + sh.n1) * sh.Kpad * 2 + (size_t)kLtRows * sh.Kpad * 2;
+}
+
+__global__ void __launch_bounds__(kLtThreads, 1)
+    k_lift_tc(const uint32_t* __restrict__ src, size_t src_pstride, size_t src_bstride, uint32_t* __restrict__ dst,
+              size_t dst_pstride, size_t dst_bstride, LtShape sh, int N, const uint16_t* __restrict__ bmat,
+              const uint32_t* __restrict__ qtab, const uint32_t* __restrict__ qinv,
+              const uint64_t* __restrict__ offL) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = sh.r, L = sh.L, Kpad = sh.Kpad;
+  const int kcols = Kpad / 8;                       // core-matrix columns along K
+  const uint32_t sbo = (uint32_t)kcols * 128u;      // bytes between 8-row groups
+  const int nrows = sh.n0 + sh.n1;
+  const int nh = sh.n1 > 0 ? 2 : 1;
+  uint4* PC = reinterpret_cast<uint4*>(smem + 512);            // per prime {q, q^-1 mod 2^32, K lo, K hi}
+  uint8_t* B = smem + 512 + 16 * 128;
+  uint8_t* A = B + (size_t)nrows * Kpad * 2;
+  const uint32_t bar0 = smem_addr(smem);
+  const uint32_t a_full = bar0, a_empty = bar0 + 8;
+  auto acc_full = [&](int h) { return bar0 + 16u + 8u * h; };
+  auto acc_empty = [&](int h) { return bar0 + 32u + 8u * h; };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 256);
+  auto tile_of = [&](int t, int& n0, int& poly, int& b) {
+    const int py = t / sh.nblk;
+    n0 = (t - py * sh.nblk) * kLtRows;
+    poly = py % sh.npoly;
+    b = py / sh.npoly;
+  };
+
+  if (tid == 0) {
+    mbar_init(a_full, 32 * kLtYWarps);
+    mbar_init(a_empty, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(acc_full(h), 1);
+      mbar_init(acc_empty(h), 32 * kLtEWarps / 2);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // resident constants: B rows (i, a) for i < r (zero above), per-prime reduction constants
+  for (int idx = tid; idx < nrows * kcols; idx += kLtThreads) {
+    const int p = idx / kcols, kc = idx - p * kcols;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (p < 4 * r)
+      v = __ldg(reinterpret_cast<const uint4*>(bmat) + (((size_t)(p >> 3) * (4 * kMaxLiftLimbs / 8) + kc) * 8 + (p & 7)));
+    *reinterpret_cast<uint4*>(B + ((size_t)((p >> 3) * kcols + kc) * 8 + (p & 7)) * 16) = v;
+  }
+  for (int i = tid; i < r; i += kLtThreads) {
+    const uint64_t k = __ldg(offL + i);
+    PC[i] = make_uint4(__ldg(qtab + i), __ldg(qinv + i), (uint32_t)k, (uint32_t)(k >> 32));
+  }
+  // K padding of the digit tile stays zero
+  for (int idx = tid; idx < kLtRows * kcols; idx += kLtThreads) {
+    const int t = idx / kcols, kc = idx - t * kcols;
+    if (kc >= (L + 1) / 2)
+      *reinterpret_cast<uint4*>(A + (size_t)(t >> 3) * sbo + kc * 128 + (t & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == kLtWarpMma) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
+                 "r"(sh.acc_cols * nh)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == kLtWarpMma) {
+    if (lane == 0) {
+      const int KS = Kpad / 16;
+      const uint32_t idesc0 = (1u << 4) | (((uint32_t)sh.n0 >> 3) << 17) | ((uint32_t)(kLtRows >> 4) << 24);
+      const uint32_t idesc1 = (1u << 4) | (((uint32_t)sh.n1 >> 3) << 17) | ((uint32_t)(kLtRows >> 4) << 24);
+      const uint64_t adesc = tc_desc(smem_addr(A), 128u, sbo);
+      const uint64_t bdesc0 = tc_desc(smem_addr(B), 128u, sbo);
+      const uint64_t bdesc1 = bdesc0 + (uint64_t)(((uint32_t)(sh.n0 >> 3) * sbo) >> 4);
+      int tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
+        if (!(ok = mbar_wait(a_full, (uint32_t)tl & 1u))) break;
+        for (int h = 0; h < nh; ++h) {
+          if (tl >= 1 && !(ok = mbar_wait(acc_empty(h), (uint32_t)(tl - 1) & 1u))) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(h * sh.acc_cols);
+          const uint64_t bd = h ? bdesc1 : bdesc0;
+          const uint32_t id = h ? idesc1 : idesc0;
+          for (int ks = 0; ks < KS; ++ks)
+            tc_mma(d, adesc + (uint64_t)(16 * ks), bd + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
+          tc_commit(acc_full(h));
+        }
+        if (!ok) break;
+        tc_commit(a_empty);
+      }
+    }
+  } else if (warp < kLtYWarps) {
+    // Y: thread (t, hh) owns limb pairs [hh PH, min(P2, (hh + 1) PH)) of coefficient t
+    const int t0 = tid & (kLtRows - 1), hh = tid >> 7;
+    const int P2 = (L + 1) / 2, PH = (P2 + 1) / 2;
+    const int p0 = hh * PH, np = max(0, min(P2, p0 + PH) - p0);
+    uint8_t* arow = A + (size_t)(t0 >> 3) * sbo + (t0 & 7) * 16;
+    uint32_t xv[32];
+    auto load = [&](int t) {
+      int n0, poly, b;
+      tile_of(t, n0, poly, b);
+      const uint32_t* s = src + (size_t)b * src_bstride + (size_t)poly * src_pstride + n0 + t0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int l = 2 * p0 + j;
+        xv[j] = (j < 2 * np && l < L) ? __ldg(s + (size_t)l * N) : 0u;
+      }
+    };
+    int tl = 0;
+    bool ok = true;
+    if (blockIdx.x < sh.ntiles) load(blockIdx.x);
+    for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
+      if (tl >= 1 && !(ok = mbar_wait(a_empty, (uint32_t)(tl - 1) & 1u))) break;
+#pragma unroll
+      for (int jp = 0; jp < 16; ++jp) {
+        if (jp < np) {
+          uint32_t d[4];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            // byte b -> f16 (1024 + b) - 1152 = b - 128; a limb beyond L contributes no digits
+            const uint32_t x = xv[2 * jp + u];
+            const uint32_t lo = __byte_perm(x, 0x64646464u, 0x5140), hi = __byte_perm(x, 0x64646464u, 0x5342);
+            asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u]) : "r"(lo), "r"(0x64806480u));
+            asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u + 1]) : "r"(hi), "r"(0x64806480u));
+            if (2 * (p0 + jp) + u >= L) d[2 * u] = d[2 * u + 1] = 0u;
+          }
+          *reinterpret_cast<uint4*>(arow + (p0 + jp) * 128) = make_uint4(d[0], d[1], d[2], d[3]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive(a_full);
+      if (t + (int)gridDim.x < sh.ntiles) load(t + gridDim.x);  // in flight while the MMAs read A
+    }
+  } else {
+    // E: group g (0..3) drains half g >> 1, 4-residue column blocks of parity g & 1
+    const int e = tid - 32 * kLtYWarps;
+    const int g = e >> 7, ec = e & (kLtRows - 1);
+    const int h = g >> 1, par = g & 1;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int i0 = h ? sh.r0 : 0, i1 = h ? r : min(r, sh.r0);
+    int tl = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
+      if (h >= nh) break;
+      int n0, poly, b;
+      tile_of(t, n0, poly, b);
+      ok = ok && mbar_wait(acc_full(h), (uint32_t)tl & 1u);
+      ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = tmem + lane_off + (uint32_t)(h * sh.acc_cols);
+      uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n0 + ec;
+      for (int q4 = par; 4 * q4 < i1 - i0; q4 += 2) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(base + 16u * (uint32_t)q4));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = i0 + 4 * q4 + j;
+          if (i < i1) {
+            // exact integers |S| < 2^22: the low mantissa bits of S + 1.5 2^23
+            int sv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sv[a] = __float_as_int(__uint_as_float(v[4 * j + a]) + 12582912.0f) - 0x4B400000;
+            const int lo = sv[0] + sv[1] * 256, hi = sv[2] + sv[3] * 256;  // |.| < 2^31
+            const uint4 k = PC[i];
+            const uint64_t u = (uint64_t)((long long)lo + ((long long)hi << 16)) +
+                               (((uint64_t)k.w << 32) | k.z);  // >= 0, < 2^49
+            // Montgomery: (u - m q) / 2^32 with m = u q^-1 mod 2^32, in (-q, 2^17)
+            const uint32_t m = (uint32_t)u * k.y;
+            int32_t res = (int32_t)((uint32_t)(u >> 32) - __umulhi(m, k.x));
+            if (res < 0) res += (int32_t)k.x;
+            d[(size_t)i * N] = (uint32_t)res;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(acc_empty(h));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == kLtWarpMma) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(sh.acc_cols * nh)
+                 : "memory");
+  }
+}
+
+// Tensor-core lift when it applies (L < 64, r <= 128, N a multiple of 128, shared memory fits);
+// returns 1 if launched, 0 if the caller must use the integer form.
+static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t sp, size_t sb, uint32_t* dst,
+                          size_t dp, size_t db, int npoly, int nbatch, int r, cudaStream_t st) {
+  const int N = ctx->N;
+  if (!ctx->d_lift_tc || ctx->crt_mode != 0 || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
+  LtShape sh;
+  sh.r = r;
+  sh.L = L;
+  sh.Kpad = 16 * ((4 * L + 15) / 16);
+  sh.r0 = 4 * ((r + 7) / 8);  // a multiple of 4, so the first half's N is a multiple of 16
+  sh.n0 = 4 * sh.r0;
+  sh.n1 = r > sh.r0 ? 16 * ((4 * (r - sh.r0) + 15) / 16) : 0;
+  sh.acc_cols = 32;
+  while (sh.acc_cols < sh.n0 || sh.acc_cols < sh.n1) sh.acc_cols <<= 1;
+  sh.nblk = N / kLtRows;
+  sh.npoly = npoly;
+  sh.ntiles = sh.nblk * npoly * nbatch;
+  if (sh.n0 % 16 || sh.n0 > 256 || sh.n1 > 256) return 0;
+  const size_t smem = lt_smem_bytes(sh);
+  if (smem > 227 * 1024) return 0;
+  static thread_local int configured_dev = -1, nsm = 0;
+  if (configured_dev != ctx->device) {
+    cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    configured_dev = ctx->device;
+  }
+  const int grid = sh.ntiles < nsm ? sh.ntiles : nsm;
+  k_lift_tc<<<grid, kLtThreads, smem, st>>>(src, sp, sb, dst, dp, db, sh, N, ctx->d_lift_tc, ctx->d_q, ctx->d_qinv,
+                                            ctx->d_lift_off + (size_t)L * ctx->R);
+  return 1;
+}
+
+// Device status word of this file's kernels: nonzero (then cleared) after a bounded wait gave up.
+unsigned int read_lift_status() {
+  unsigned int v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_lift_dev_status, sizeof(v)) != cudaSuccess) return 0;
+  if (v) cudaMemcpyToSymbol(g_lift_dev_status, &z, sizeof(z));
+  return v;
+}
+
 template <int LB>
 static void lift_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t sp, size_t sb, uint32_t* dst,
                         size_t dp, size_t db, int npoly, int nbatch, int r, cudaStream_t st) {
@@ -179,6 +455,8 @@ int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstri
     return FHE_EINVAL;
   }
   ProfScope ps(ctx, FHE_K_LIFT, 1, st);
+  if (lift_tc_launch(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, npoly, nbatch, r, st))
+    return FHE_OK;
 #define FHE_LIFT_CASE(B)                                                                 \
   if (L <= B) {                                                                          \
     lift_launch<B>(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, \

@@ -250,6 +250,45 @@ static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const s
   return (ctx->d_crt_tc = upload(ctx, mat)) ? FHE_OK : FHE_ENOMEM;
 }
 
+// Tensor-core form of the lift (k_lift_tc).  With x = sum_k b_k 256^k (bytes
+// b_k of the limbs) and d_k = b_k - 128, the residue row i of the GEMM output
+// is T_i = sum_a 256^a sum_k d_k c_{i,k,a}, c_{i,k,a} the digits of
+// C_{i,k} = 2^(8k) 2^32 mod q_i; T_i = (x - 128 sum_k 256^k) 2^32 (mod q_i), so
+// adding off_i(L) = (128 sum_{k<4L} 256^k) 2^32 mod q_i (and 2^17 q_i to make
+// it non-negative) and one Montgomery reduction give x mod q_i.
+static int build_lift_tc(fhe_ctx* ctx) {
+  const int R = ctx->R, KMAX = 4 * kMaxLiftLimbs;
+  const std::vector<uint32_t>& q = ctx->q;
+  const size_t rows8 = (size_t)((4 * R + 7) / 8) * 8;  // whole 8-row core-matrix groups
+  std::vector<uint16_t> mat(rows8 * KMAX, 0);
+  std::vector<uint64_t> off((size_t)(kMaxLiftLimbs + 1) * R, 0);
+  for (int i = 0; i < R; ++i) {
+    const uint64_t qi = q[i];
+    uint64_t c = ((uint64_t)1 << 32) % qi;  // C_{i,0} = 2^32 mod q
+    uint64_t offacc = 0;                    // (128 sum_{k' < k} 256^k') 2^32 mod q
+    for (int k = 0; k < KMAX; ++k) {
+      if ((k & 3) == 0) off[(size_t)(k >> 2) * R + i] = offacc + (qi << 17);
+      // digits of C: bytes 0..2 balanced with carry, byte 3 takes the carry (C < 2^31)
+      int carry = 0, dg[4];
+      for (int a = 0; a < 3; ++a) {
+        const int v = (int)((c >> (8 * a)) & 0xFF) + carry;
+        carry = v >= 128 ? 1 : 0;
+        dg[a] = v - 256 * carry;
+      }
+      dg[3] = (int)((c >> 24) & 0xFF) + carry;
+      for (int a = 0; a < 4; ++a) {
+        const int row = 4 * i + a;
+        mat[(((size_t)(row >> 3) * (KMAX / 8) + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7)] = half_of_int(dg[a]);
+      }
+      offacc = (offacc + 128 * c) % qi;
+      c = (c << 8) % qi;
+    }
+    off[(size_t)kMaxLiftLimbs * R + i] = offacc + (qi << 17);
+  }
+  if (!(ctx->d_lift_tc = upload(ctx, mat)) || !(ctx->d_lift_off = upload(ctx, off))) return FHE_ENOMEM;
+  return FHE_OK;
+}
+
 int build_tables(fhe_ctx* ctx) {
   const int N = ctx->N, logN = ctx->prm.logN, R = ctx->R;
   const auto& gp = global_primes();
@@ -386,6 +425,7 @@ int build_tables(fhe_ctx* ctx) {
   }
   if (!(ctx->d_crt_dig = upload(ctx, dig))) return FHE_ENOMEM;
   if (build_crt_tc(ctx, qhat, negm) != FHE_OK) return FHE_ENOMEM;
+  if (build_lift_tc(ctx) != FHE_OK) return FHE_ENOMEM;
   if (!(ctx->d_crt_qhat = upload(ctx, qhat)) || !(ctx->d_crt_inv = upload(ctx, crt_inv)) ||
       !(ctx->d_crt_negm = upload(ctx, negm)) || !(ctx->d_invq = upload(ctx, invq)))
     return FHE_ENOMEM;

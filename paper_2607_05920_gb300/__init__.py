@@ -209,14 +209,19 @@ class Context:
 
     # ---------------------------------------------------------------- memory
     def workspace(self, op: int, logQ: int, cnum: int):
-        """A cached device workspace large enough for `op` at (logQ, cnum)."""
+        """A cached device workspace large enough for `op` at (logQ, cnum), one per stream: calls
+        on different streams may run concurrently only with different workspaces."""
         nbytes = lib.fhe_workspace_bytes(self.handle, op, int(logQ), int(cnum))
         if nbytes == 0:
             raise FheError(FHE_EINVAL, "fhe_workspace_bytes")
-        cur = self._ws.get(op)
+        stream = self._torch.cuda.current_stream()
+        key = (op, stream.cuda_stream)
+        cur = self._ws.get(key)
         if cur is None or cur.numel() < nbytes:
+            if cur is not None:
+                cur.record_stream(stream)  # the old buffer may still be in use by queued work
             cur = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device=self.device)
-            self._ws[op] = cur
+            self._ws[key] = cur
         return cur
 
     def bgv_bits(self, level: int) -> int:

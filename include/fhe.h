@@ -107,7 +107,7 @@ typedef struct {
 } fhe_ct;
 
 /* Create a context for one ring size and modulus chain.  Computes the NTT
- * primes (30/31-bit, q = 1 mod 2N; Sec. 4) and the precomputed tables of
+ * primes (30-bit, q = 1 mod 2N; Sec. 4) and the precomputed tables of
  * Sec. 5 "Precomputation" (bit-reversed psi powers and their inverses,
  * 2^(32 l) mod q_i, Garner constants [q_j^-1]_{q_k}, prod_{i<k} q_i) and
  * uploads them.  `alloc`/`free_` may both be NULL (cudaMalloc/cudaFree).

@@ -156,7 +156,7 @@ inline int limbs_for_bits(int bits) { return (bits + 31) / 32; }
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------ device arithmetic
-// All primes satisfy 2^30 < q < 2^31, so 2q < 2^32.
+// All primes satisfy 2^29 < q < 2^30, so 4q < 2^32.
 
 // a * w mod q with w's Shoup companion wp = floor(w 2^32 / q); any a < 2^32.
 // Result in [0, q).  (Shoup's precomputed-quotient multiplication.)
@@ -183,7 +183,7 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t q,
 }
 
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t q) {
-  uint32_t s = a + b;  // a, b < q < 2^31: no overflow
+  uint32_t s = a + b;  // a, b < q < 2^30: no overflow
   return s >= q ? s - q : s;
 }
 __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) {

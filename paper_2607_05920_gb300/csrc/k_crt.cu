@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
 // product: one 32x32->64 multiply-add per (prime, limb), with the constant
 // rows staged in shared memory and read as 128-bit broadcasts.
 // Column form of the dense product: the constants are held as 24-bit digits,
-// so each product y_i d (y_i < 2^31, d < 2^24) is below 2^55 and a whole
+// so each product y_i d (y_i < q < 2^30, d < 2^24) is below 2^54 and a whole
 // column sum over r + 1 <= 257 terms fits one 64-bit register -- one
 // 32x32->64 multiply-add per (prime, digit), no carry chain.  The y_i sit in
 // the thread's shared-memory column; columns are taken 8 at a time (192 bits
@@ -375,7 +375,7 @@ constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
 constexpr int kTcHead = 1024;               // mbarriers + TMEM address
 constexpr int kTcFsx = 2048;                // quotient partial sums, [tile parity][half][row]
 
-// Balanced bytes of y < 2^31 as two f16x2 registers {d0, d1}, {d2, d3}:
+// Balanced bytes of y < 2^31 (y < q) as two f16x2 registers {d0, d1}, {d2, d3}:
 // e = y + 0x808080, d_a = byte_a(e) - 128 for a < 3, d_3 = byte_3(e) <= 128.
 // A byte b is placed under the f16 exponent of 1024 (bits 0x6400 | b = 1024 + b),
 // then 1152 (or 1024) is subtracted exactly.

@@ -142,10 +142,10 @@ __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint
   if (n >= N) return;
   const int b = blockIdx.y;
   const int32_t v = (int32_t)src[(size_t)b * src_bstride + n];
-  const uint32_t av = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;  // < 2^31 < 2q
+  const uint32_t av = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;  // <= 2^31
   for (int i = 0; i < r; ++i) {
     const uint32_t q = __ldg(qtab + i);
-    uint32_t m = av >= q ? av - q : av;
+    uint32_t m = av < q ? av : av % q;
     if (v < 0 && m != 0) m = q - m;
     dst[(size_t)b * dst_bstride + (size_t)i * N + n] = m;
   }

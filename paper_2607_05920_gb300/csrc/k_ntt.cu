@@ -22,16 +22,29 @@ namespace fhe {
 
 constexpr int kRowLen = 256;   // N2
 
+// Lazy butterflies (Harvey, "Faster arithmetic for number-theoretic
+// transforms", 2014): with q < 2^30, 4q fits a word, so values travel between
+// stages only partly reduced and each butterfly does one conditional
+// subtraction.  Forward (CT): x, y in [0, 4q) -> [0, 4q).  Inverse (GS):
+// x, y in [0, 2q) -> [0, 2q).  Shoup products with a lazy result in [0, 2q).
 __device__ __forceinline__ void ct_bfly(uint32_t& x, uint32_t& y, uint32_t w, uint32_t wp, uint32_t q) {
-  uint32_t v = shoup_mul(y, w, wp, q);
-  uint32_t u = x;
-  x = add_mod(u, v, q);
-  y = sub_mod(u, v, q);
+  const uint32_t q2 = 2u * q;
+  const uint32_t u = x >= q2 ? x - q2 : x;          // [0, 2q)
+  const uint32_t t = shoup_mul_lazy(y, w, wp, q);   // [0, 2q)
+  x = u + t;                                        // [0, 4q)
+  y = u - t + q2;                                   // (0, 4q)
 }
 __device__ __forceinline__ void gs_bfly(uint32_t& x, uint32_t& y, uint32_t w, uint32_t wp, uint32_t q) {
-  uint32_t u = x, v = y;
-  x = add_mod(u, v, q);
-  y = shoup_mul(u + q - v, w, wp, q);  // u - v + q < 2q < 2^32
+  const uint32_t q2 = 2u * q;
+  const uint32_t s = x + y;                         // [0, 4q)
+  const uint32_t d = x - y + q2;                    // (0, 4q)
+  x = s >= q2 ? s - q2 : s;                         // [0, 2q)
+  y = shoup_mul_lazy(d, w, wp, q);                  // [0, 2q)
+}
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t q) {
+  x = x >= 2u * q ? x - 2u * q : x;
+  return x >= q ? x - q : x;
 }
 
 // ---------------------------------------------------------------- one CTA
@@ -68,7 +81,7 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
       }
       __syncthreads();
     }
-    for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = s[j];
+    for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = reduce4(s[j], q);
   } else {
     for (int h = half, lt = 0; h >= 1; h >>= 1, ++lt) {
       for (int b = threadIdx.x; b < half; b += blockDim.x) {
@@ -244,7 +257,9 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __r
   }
   uint4* a4 = reinterpret_cast<uint4*>(a + 16 * j0);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) a4[v] = make_uint4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+  for (int v = 0; v < 4; ++v)
+    a4[v] = make_uint4(reduce4(x[4 * v], q), reduce4(x[4 * v + 1], q), reduce4(x[4 * v + 2], q),
+                       reduce4(x[4 * v + 3], q));
 }
 
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __restrict__ data, RowMap rm, int r,

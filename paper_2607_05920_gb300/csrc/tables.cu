@@ -65,14 +65,15 @@ static bool is_prime32(uint32_t n) {
 static uint32_t inv_mod(uint32_t a, uint32_t q) { return (uint32_t)powmod64(a, q - 2, q); }
 static uint32_t shoup_of(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
 
-// Primes q = 1 (mod 2^17), 2^30 < q < 2^31, largest first: NTT-friendly for
-// every N <= 2^16 (Sec. 2: q = 1 mod 2N; Sec. 4: 30-31-bit primes).
+// Primes q = 1 (mod 2^17), 2^29 < q < 2^30, largest first: NTT-friendly for
+// every N <= 2^16 (Sec. 2: q = 1 mod 2N; Sec. 4: 30-bit primes).  Below 2^30,
+// 4q fits 32 bits, which the lazy NTT butterflies use.
 const std::vector<uint32_t>& global_primes() {
   static std::vector<uint32_t> primes;
   static std::once_flag once;
   std::call_once(once, [] {
     const uint32_t step = 1u << 17;
-    for (uint32_t c = 0x80000000u - step + 1; c > 0x40000000u && (int)primes.size() < kMaxPrimes; c -= step)
+    for (uint32_t c = 0x40000000u - step + 1; c > 0x20000000u && (int)primes.size() < kMaxPrimes; c -= step)
       if (is_prime32(c)) primes.push_back(c);
   });
   return primes;
@@ -268,7 +269,7 @@ static int build_lift_tc(fhe_ctx* ctx) {
     uint64_t offacc = 0;                    // (128 sum_{k' < k} 256^k') 2^32 mod q
     for (int k = 0; k < KMAX; ++k) {
       if ((k & 3) == 0) off[(size_t)(k >> 2) * R + i] = offacc + (qi << 17);
-      // digits of C: bytes 0..2 balanced with carry, byte 3 takes the carry (C < 2^31)
+      // digits of C: bytes 0..2 balanced with carry, byte 3 takes the carry (C < q < 2^30)
       int carry = 0, dg[4];
       for (int a = 0; a < 3; ++a) {
         const int v = (int)((c >> (8 * a)) & 0xFF) + carry;

@@ -38,14 +38,14 @@ def test_host_helpers_without_gpu():
     assert fhe.lib.fhe_ct_bytes(16, 1200, 1) == 2 * 38 * 65536 * 4
     assert fhe.lib.fhe_ct_bytes(11, 120, 3) == 3 * 2 * 4 * 2048 * 4
     assert fhe.lib.fhe_ct_bytes(17, 120, 1) == 0
-    # prime counts: prod of all but the top prime covers 2^bound (primes in (2^30, 2^31))
+    # prime counts: prod of all but the top prime covers 2^bound (primes in (2^29, 2^30))
     for bits in (1, 30, 31, 100, 1217, 2417, 3616):
         r = fhe.fhe_primes_for_bound(bits)
         assert r >= 2
-        assert 30 * (r - 1) >= bits or 31 * (r - 1) >= bits
-        assert 31 * (r - 2) < bits + 31
-    assert fhe.fhe_primes_for_bound(3616) == 118  # relinearisation at N=2^16, logQ=logP=1200
-    assert fhe.fhe_primes_for_bound(2417) == 80   # Karatsuba tensor product, same ring
+        assert 30 * (r - 1) >= bits
+        assert 29 * (r - 2) < bits
+    assert fhe.fhe_primes_for_bound(3616) == 123  # relinearisation at N=2^16, logQ=logP=1200
+    assert fhe.fhe_primes_for_bound(2417) == 82   # Karatsuba tensor product, same ring
 
 
 def test_ctx_create_rejects_bad_params_before_touching_the_device():

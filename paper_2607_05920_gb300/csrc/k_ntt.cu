@@ -211,23 +211,12 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restric
 constexpr int kRowsPerCta = 8;
 __device__ __forceinline__ int rpad(int pos) { return pos + (pos >> 4); }
 
-__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __restrict__ data, RowMap rm, int r,
-                                                                   int logN, const uint32_t* __restrict__ tw,
-                                                                   const uint32_t* __restrict__ twp,
-                                                                   const uint32_t* __restrict__ qtab) {
-  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
-  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
-  const int N = 1 << logN;
-  const int p = rm.prime_of(blockIdx.y, r);
-  const uint32_t q = __ldg(qtab + p);
-  const uint32_t* w = tw + (size_t)p * N;
-  const uint32_t* wp = twp + (size_t)p * N;
-  const int c = blockIdx.x * kRowsPerCta + sub;  // matrix row
-  uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c * kRowLen;
-  uint32_t* sr = s + sub * (kRowLen + kRowLen / 16);
-  uint32_t x[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
+// Forward row pass on one matrix row held by 16 threads: x[k] = row[j0 + 16 k]
+// on entry; on exit x[j] = row[16 j0 + j] of the transform, reduced to [0, q).
+// sr: the row's padded shared-memory slot; the 16 threads are half a warp.
+__device__ __forceinline__ void rows_fwd_core(uint32_t (&x)[16], int c, int j0, uint32_t* sr, int N,
+                                              const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                              uint32_t q) {
   // layout A: distance t = 16 h, stage index N/(2t), group c (8/h) + k/(2h)
 #pragma unroll
   for (int h = 8; h >= 1; h >>= 1) {
@@ -255,11 +244,118 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __r
       ct_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
     }
   }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = reduce4(x[j], q);
+}
+
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __restrict__ data, RowMap rm, int r,
+                                                                   int logN, const uint32_t* __restrict__ tw,
+                                                                   const uint32_t* __restrict__ twp,
+                                                                   const uint32_t* __restrict__ qtab) {
+  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int p = rm.prime_of(blockIdx.y, r);
+  const uint32_t q = __ldg(qtab + p);
+  const int c = blockIdx.x * kRowsPerCta + sub;  // matrix row
+  uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c * kRowLen;
+  uint32_t x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
+  rows_fwd_core(x, c, j0, s + sub * (kRowLen + kRowLen / 16), N, tw + (size_t)p * N, twp + (size_t)p * N, q);
   uint4* a4 = reinterpret_cast<uint4*>(a + 16 * j0);
 #pragma unroll
-  for (int v = 0; v < 4; ++v)
-    a4[v] = make_uint4(reduce4(x[4 * v], q), reduce4(x[4 * v + 1], q), reduce4(x[4 * v + 2], q),
-                       reduce4(x[4 * v + 3], q));
+  for (int v = 0; v < 4; ++v) a4[v] = make_uint4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+}
+
+// Forward row pass of the four operand transforms (B1, A1, B2, A2) of a
+// Karatsuba tensor product, fused with its pointwise products (Sec. 5
+// "Karatsuba Polynomial Multiplication"): D0 = B1 B2, D2 = A1 A2,
+// D1 = (A1 + B1)(A2 + B2) - D0 - D2 (Montgomery products), written over the
+// B1, A1, B2 rows.  X = [batch][4][r][N].  A CTA takes two matrix rows of one
+// (batch, prime) for all four operands: 4 x 2 rows x 16 threads.
+constexpr int kKaraRows = 2;
+__global__ void __launch_bounds__(64 * kKaraRows) k_ntt_rows_fwd_kara(uint32_t* __restrict__ X, int r, int logN,
+                                                                      const uint32_t* __restrict__ tw,
+                                                                      const uint32_t* __restrict__ twp,
+                                                                      const uint32_t* __restrict__ qtab,
+                                                                      const uint32_t* __restrict__ qinv) {
+  constexpr int SLOT = kRowLen + kRowLen / 16;
+  __shared__ uint32_t s[4 * kKaraRows * SLOT];
+  const int pi = threadIdx.x / (16 * kKaraRows), sub = (threadIdx.x >> 4) % kKaraRows, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const size_t rowN = (size_t)r * N;
+  uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N;
+  const int c = blockIdx.x * kKaraRows + sub;
+  uint32_t* a = base + (size_t)pi * rowN + (size_t)c * kRowLen;
+  uint32_t* sr = s + (pi * kKaraRows + sub) * SLOT;
+  uint32_t x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
+  rows_fwd_core(x, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+  __syncwarp();  // every thread of the row is done reading the exchange slot
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sr[rpad(16 * j0 + j)] = x[j];
+  __syncthreads();
+  // Karatsuba on four consecutive positions per thread
+  const int kr = threadIdx.x / 64, pos = (threadIdx.x & 63) * 4;
+  const uint32_t* s0 = s + (0 * kKaraRows + kr) * SLOT;  // B1
+  const uint32_t* s1 = s + (1 * kKaraRows + kr) * SLOT;  // A1
+  const uint32_t* s2 = s + (2 * kKaraRows + kr) * SLOT;  // B2
+  const uint32_t* s3 = s + (3 * kKaraRows + kr) * SLOT;  // A2
+  uint32_t d0[4], d1[4], d2[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int sp = rpad(pos + u);
+    const uint32_t B1 = s0[sp], A1 = s1[sp], B2 = s2[sp], A2 = s3[sp];
+    d0[u] = mont_mul(B1, B2, q, qi);
+    d2[u] = mont_mul(A1, A2, q, qi);
+    const uint32_t t = mont_mul(add_mod(A1, B1, q), add_mod(A2, B2, q), q, qi);
+    d1[u] = sub_mod(sub_mod(t, d0[u], q), d2[u], q);
+  }
+  const size_t off = (size_t)(blockIdx.x * kKaraRows + kr) * kRowLen + pos;
+  *reinterpret_cast<uint4*>(base + off) = make_uint4(d0[0], d0[1], d0[2], d0[3]);
+  *reinterpret_cast<uint4*>(base + rowN + off) = make_uint4(d1[0], d1[1], d1[2], d1[3]);
+  *reinterpret_cast<uint4*>(base + 2 * rowN + off) = make_uint4(d2[0], d2[1], d2[2], d2[3]);
+}
+
+// Forward row pass of the lifted polynomial of a key switch fused with its
+// products with the key (Sec. 6): Y = [batch][2][r][N], block 0 transformed
+// and multiplied by the key rows K[0][k], K[1][k] (NTT form), the two
+// Montgomery products written to blocks 0 and 1.
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd_key(uint32_t* __restrict__ Y,
+                                                                       const uint32_t* __restrict__ K, int krows,
+                                                                       int r, int logN,
+                                                                       const uint32_t* __restrict__ tw,
+                                                                       const uint32_t* __restrict__ twp,
+                                                                       const uint32_t* __restrict__ qtab,
+                                                                       const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const int c = blockIdx.x * kRowsPerCta + sub;
+  const size_t coff = (size_t)c * kRowLen;
+  uint32_t* a = Y + ((size_t)b * 2 * r + p) * N + coff;
+  uint32_t x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
+  rows_fwd_core(x, c, j0, s + sub * (kRowLen + kRowLen / 16), N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+  const uint4* kb = reinterpret_cast<const uint4*>(K + (size_t)p * N + coff + 16 * j0);
+  const uint4* ka = reinterpret_cast<const uint4*>(K + (size_t)(krows + p) * N + coff + 16 * j0);
+  uint4* o0 = reinterpret_cast<uint4*>(a + 16 * j0);
+  uint4* o1 = reinterpret_cast<uint4*>(Y + ((size_t)b * 2 * r + r + p) * N + coff + 16 * j0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 vb = __ldg(kb + v), va = __ldg(ka + v);
+    o0[v] = make_uint4(mont_mul(x[4 * v], vb.x, q, qi), mont_mul(x[4 * v + 1], vb.y, q, qi),
+                       mont_mul(x[4 * v + 2], vb.z, q, qi), mont_mul(x[4 * v + 3], vb.w, q, qi));
+    o1[v] = make_uint4(mont_mul(x[4 * v], va.x, q, qi), mont_mul(x[4 * v + 1], va.y, q, qi),
+                       mont_mul(x[4 * v + 2], va.z, q, qi), mont_mul(x[4 * v + 3], va.w, q, qi));
+  }
 }
 
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __restrict__ data, RowMap rm, int r,
@@ -350,6 +446,54 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
     switch (logN1) { FHE_NTT_COLS(5) FHE_NTT_COLS(6) FHE_NTT_COLS(7) FHE_NTT_COLS(8) }
   }
 #undef FHE_NTT_COLS
+  return FHE_OK;
+}
+
+static void cols_fwd_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, cudaStream_t st) {
+  const int logN = ctx->prm.logN, logN1 = logN - 8;
+  dim3 gcols(kRowLen / 32, rows);
+#define FHE_NTT_COLS_F(L)                                                                          \
+  case L:                                                                                          \
+    k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q); \
+    break;
+  switch (logN1) { FHE_NTT_COLS_F(5) FHE_NTT_COLS_F(6) FHE_NTT_COLS_F(7) FHE_NTT_COLS_F(8) }
+#undef FHE_NTT_COLS_F
+}
+
+// Forward transforms of X = [nbatch][4][r][N] and the Karatsuba products,
+// leaving D0, D1, D2 in blocks 0..2 (the row pass carries the products).
+int launch_ntt_fwd_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st) {
+  const int logN = ctx->prm.logN, N = ctx->N;
+  if (logN <= 12 || (size_t)nbatch * 4 * r > 65535u || (size_t)nbatch * r > 65535u) {
+    int rc = launch_ntt(ctx, X, nbatch * 4, r, r, r, false, st);
+    return rc ? rc : launch_pointwise_tensor(ctx, X, r, nbatch, st);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_FWD, 2, st);
+    cols_fwd_launch(ctx, X, RowMap{r, r}, nbatch * 4 * r, r, st);
+    dim3 grid((N >> 8) / kKaraRows, nbatch * r);
+    k_ntt_rows_fwd_kara<<<grid, 64 * kKaraRows, 0, st>>>(X, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q,
+                                                          ctx->d_qinv);
+  }
+  return FHE_OK;
+}
+
+// Forward transform of block 0 of Y = [nbatch][2][r][N] and its products with
+// the key K = [2][krows][N] (NTT form) into blocks 0 and 1.
+int launch_ntt_fwd_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
+                       cudaStream_t st) {
+  const int logN = ctx->prm.logN, N = ctx->N;
+  if (logN <= 12 || (size_t)nbatch * r > 65535u) {
+    int rc = launch_ntt(ctx, Y, nbatch, r, 2 * r, r, false, st);
+    return rc ? rc : launch_pointwise_key(ctx, Y, K, krows, r, nbatch, st);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_FWD, 2, st);
+    cols_fwd_launch(ctx, Y, RowMap{r, 2 * r}, nbatch * r, r, st);
+    dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
+    k_ntt_rows_fwd_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q,
+                                                          ctx->d_qinv);
+  }
   return FHE_OK;
 }
 

@@ -213,14 +213,20 @@ def step_work(fhe, cnum: int, crt_mode: str) -> dict:
     rt = fhe.fhe_primes_for_bound(LOGN + 2 * LOGQ + 1)
     rk = fhe.fhe_primes_for_bound(LOGN + LOGQ + LOGP + LOGQ)
     lq_relin = (LOGQ + LOGP + 31) // 32
-    bfly = N // 2 * LOGN
+    # N > 2^12: the column stages (log N - 8 of them) run in the NTT passes, the
+    # 8 row stages of both directions and the products in the fused pass
+    col_st = LOGN - 8 if LOGN > 12 else LOGN
+    row_bfly = N // 2 * (LOGN - col_st)
+    col_bfly = N // 2 * col_st
+    pw = cnum * N * (3 * rt + 2 * rk) * 6
     return {
         "crt": cnum * N * (3 * cs(rt, L) + 2 * cs(rk, lq_relin)),
-        "ntt_fwd": cnum * (4 * rt + rk) * bfly * 4,
-        "ntt_inv": cnum * (3 * rt + 2 * rk) * (bfly * 4 + N * 4),
+        "ntt_fwd": cnum * (4 * rt + rk) * col_bfly * 4,
+        "ntt_inv": cnum * (3 * rt + 2 * rk) * (col_bfly * 4 + N * 4),
+        "ntt_pw": cnum * (7 * rt + 3 * rk) * row_bfly * 4 + (pw if LOGN > 12 else 0),
         "lift": (cnum * N * (4 * lift_flops_tc(rt, L) + lift_flops_tc(rk, L)) if crt_mode == "direct"
                  else cnum * N * (4 * rt * L + rk * L) * 2),
-        "pointwise": cnum * N * (3 * rt + 2 * rk) * 6,
+        "pointwise": pw if LOGN <= 12 else 0,
         "primes": {"tensor": rt, "keyswitch": rk},
     }
 

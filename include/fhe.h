@@ -269,7 +269,10 @@ int fhe_mult_relin_rescale_noalloc(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* 
 #define FHE_K_POINTWISE 3 /* transform-domain products               */
 #define FHE_K_CRT 4       /* Garner reconstruction + fused epilogue  */
 #define FHE_K_LIMB 5      /* limb-domain kernels (rescale, ...)      */
-#define FHE_K_COUNT 6
+#define FHE_K_NTT_PW 6    /* fused transform-domain pass: forward row
+                             stages, pointwise products, inverse row
+                             stages of a ring product                */
+#define FHE_K_COUNT 7
 /* Reset the per-class counters of `ctx`; with enable != 0, also bracket
  * every subsequent launch with CUDA events on its stream (adds two event
  * records per launch).  Not thread-safe with concurrent calls on ctx. */

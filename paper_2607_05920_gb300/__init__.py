@@ -97,7 +97,7 @@ SIGNATURES = {
     "fhe_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
 }
 
-KERNEL_CLASSES = ("lift", "ntt_fwd", "ntt_inv", "pointwise", "crt", "limb")
+KERNEL_CLASSES = ("lift", "ntt_fwd", "ntt_inv", "pointwise", "crt", "limb", "ntt_pw")
 
 
 def _load():

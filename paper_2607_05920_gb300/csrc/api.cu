@@ -160,8 +160,7 @@ int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int n
                     const uint32_t* add, size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out,
                     cudaStream_t st, const int32_t* item_bits = nullptr, int out_limbs_pad = 0) {
   const size_t N = ctx->N;
-  RET_IF(launch_ntt_fwd_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
-  RET_IF(launch_ntt(ctx, Y, nbatch * 2, rk, rk, rk, true, st));
+  RET_IF(launch_ring_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
   EpiArgs epi;
   epi.kind = Epi::kRelin;
   epi.out_bits = logQ;
@@ -205,8 +204,7 @@ int mult_bgv(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* 
   RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
                      4 * (size_t)rt * N, 2, cnum, rt, st));
-  RET_IF(launch_ntt_fwd_tensor(ctx, X, rt, cnum, st));
-  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  RET_IF(launch_ring_tensor(ctx, X, rt, cnum, st));
   EpiArgs e0;
   e0.kind = Epi::kStore;
   e0.out_bits = 32 * nxt;
@@ -217,8 +215,7 @@ int mult_bgv(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* 
                            0, nullptr, 0, 0, 0, D, (size_t)L * N, 3 * (size_t)L * N, level, st));
   RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
                      st));
-  RET_IF(launch_ntt_fwd_key(ctx, Y, ctx->evk.ntt, ctx->evk.rows, rk, cnum, st));
-  RET_IF(launch_ntt(ctx, Y, cnum * 2, rk, rk, rk, true, st));
+  RET_IF(launch_ring_key(ctx, Y, ctx->evk.ntt, ctx->evk.rows, rk, cnum, st));
   EpiArgs e1;
   e1.kind = Epi::kStore;
   e1.out_bits = 32 * nxk;
@@ -250,8 +247,7 @@ int mult_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* ou
   RET_IF(launch_lift(ctx, a, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_lift(ctx, b, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N, 4 * (size_t)rt * N, 2,
                      cnum, rt, st));
-  RET_IF(launch_ntt_fwd_tensor(ctx, X, rt, cnum, st));
-  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  RET_IF(launch_ring_tensor(ctx, X, rt, cnum, st));
   EpiArgs e0;
   e0.kind = Epi::kStore;
   e0.out_bits = logQ_max;
@@ -311,8 +307,7 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
   RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
                      4 * (size_t)rt * N, 2, cnum, rt, st));
-  RET_IF(launch_ntt_fwd_tensor(ctx, X, rt, cnum, st));
-  RET_IF(launch_ntt(ctx, X, cnum, 3 * rt, 4 * rt, rt, true, st));
+  RET_IF(launch_ring_tensor(ctx, X, rt, cnum, st));
   EpiArgs e0;
   e0.kind = Epi::kStore;
   e0.out_bits = logQ;
@@ -736,8 +731,7 @@ int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t
   }
   RET_IF(launch_lift_small(ctx, v, true, N, Y, 2 * (size_t)re * N, cnum, re, st));
   SwitchKey pk{ctx->d_pk_ntt, re};
-  RET_IF(launch_ntt_fwd_key(ctx, Y, pk.ntt, pk.rows, re, cnum, st));
-  RET_IF(launch_ntt(ctx, Y, cnum * 2, re, re, re, true, st));
+  RET_IF(launch_ring_key(ctx, Y, pk.ntt, pk.rows, re, cnum, st));
   if (is_bgv(ctx)) {  // exact v pk, then (+ m + t e) mod Q_l
     EpiArgs ex;
     ex.kind = Epi::kStore;

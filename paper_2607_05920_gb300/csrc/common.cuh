@@ -213,11 +213,12 @@ int launch_ntt(const fhe_ctx* ctx, uint32_t* data, int ngroups, int group_rows, 
 // arithmetic, Karatsuba of Sec. 5 for the tensor).
 //  tensor: X = [nbatch][4][r][N] holding (B1, A1, B2, A2) -> (D0, D1, D2) in rows 0..3r
 int launch_pointwise_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st);
-// Forward NTTs fused with the pointwise products that follow them (row pass carries the products):
-// X = [nbatch][4][r][N] -> Karatsuba D0, D1, D2 in blocks 0..2; Y = [nbatch][2][r][N] block 0 -> (Y0 K0, Y0 K1).
-int launch_ntt_fwd_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st);
-int launch_ntt_fwd_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
-                       cudaStream_t st);
+// Ring products in the transform domain, fused (forward transforms, pointwise products, inverse transforms):
+//  tensor: X = [nbatch][4][r][N] (B1, A1, B2, A2) -> D0, D1, D2 (coefficient form) in blocks 0..2
+//  key:    Y = [nbatch][2][r][N] block 0 (D) -> D K_b in block 0, D K_a in block 1, K = [2][krows][N]
+int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st);
+int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
+                    cudaStream_t st);
 //  key: Y = [nbatch][2][r][N]; row block 0 holds D (in), outputs D*K_b into block 0 and
 //  D*K_a into block 1 with K = [2][krows][N] (first r rows used).
 int launch_pointwise_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,

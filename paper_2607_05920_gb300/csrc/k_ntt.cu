@@ -268,96 +268,6 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __r
   for (int v = 0; v < 4; ++v) a4[v] = make_uint4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
 }
 
-// Forward row pass of the four operand transforms (B1, A1, B2, A2) of a
-// Karatsuba tensor product, fused with its pointwise products (Sec. 5
-// "Karatsuba Polynomial Multiplication"): D0 = B1 B2, D2 = A1 A2,
-// D1 = (A1 + B1)(A2 + B2) - D0 - D2 (Montgomery products), written over the
-// B1, A1, B2 rows.  X = [batch][4][r][N].  A CTA takes two matrix rows of one
-// (batch, prime) for all four operands: 4 x 2 rows x 16 threads.
-constexpr int kKaraRows = 2;
-__global__ void __launch_bounds__(64 * kKaraRows) k_ntt_rows_fwd_kara(uint32_t* __restrict__ X, int r, int logN,
-                                                                      const uint32_t* __restrict__ tw,
-                                                                      const uint32_t* __restrict__ twp,
-                                                                      const uint32_t* __restrict__ qtab,
-                                                                      const uint32_t* __restrict__ qinv) {
-  constexpr int SLOT = kRowLen + kRowLen / 16;
-  __shared__ uint32_t s[4 * kKaraRows * SLOT];
-  const int pi = threadIdx.x / (16 * kKaraRows), sub = (threadIdx.x >> 4) % kKaraRows, j0 = threadIdx.x & 15;
-  const int N = 1 << logN;
-  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
-  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
-  const size_t rowN = (size_t)r * N;
-  uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N;
-  const int c = blockIdx.x * kKaraRows + sub;
-  uint32_t* a = base + (size_t)pi * rowN + (size_t)c * kRowLen;
-  uint32_t* sr = s + (pi * kKaraRows + sub) * SLOT;
-  uint32_t x[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
-  rows_fwd_core(x, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
-  __syncwarp();  // every thread of the row is done reading the exchange slot
-#pragma unroll
-  for (int j = 0; j < 16; ++j) sr[rpad(16 * j0 + j)] = x[j];
-  __syncthreads();
-  // Karatsuba on four consecutive positions per thread
-  const int kr = threadIdx.x / 64, pos = (threadIdx.x & 63) * 4;
-  const uint32_t* s0 = s + (0 * kKaraRows + kr) * SLOT;  // B1
-  const uint32_t* s1 = s + (1 * kKaraRows + kr) * SLOT;  // A1
-  const uint32_t* s2 = s + (2 * kKaraRows + kr) * SLOT;  // B2
-  const uint32_t* s3 = s + (3 * kKaraRows + kr) * SLOT;  // A2
-  uint32_t d0[4], d1[4], d2[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int sp = rpad(pos + u);
-    const uint32_t B1 = s0[sp], A1 = s1[sp], B2 = s2[sp], A2 = s3[sp];
-    d0[u] = mont_mul(B1, B2, q, qi);
-    d2[u] = mont_mul(A1, A2, q, qi);
-    const uint32_t t = mont_mul(add_mod(A1, B1, q), add_mod(A2, B2, q), q, qi);
-    d1[u] = sub_mod(sub_mod(t, d0[u], q), d2[u], q);
-  }
-  const size_t off = (size_t)(blockIdx.x * kKaraRows + kr) * kRowLen + pos;
-  *reinterpret_cast<uint4*>(base + off) = make_uint4(d0[0], d0[1], d0[2], d0[3]);
-  *reinterpret_cast<uint4*>(base + rowN + off) = make_uint4(d1[0], d1[1], d1[2], d1[3]);
-  *reinterpret_cast<uint4*>(base + 2 * rowN + off) = make_uint4(d2[0], d2[1], d2[2], d2[3]);
-}
-
-// Forward row pass of the lifted polynomial of a key switch fused with its
-// products with the key (Sec. 6): Y = [batch][2][r][N], block 0 transformed
-// and multiplied by the key rows K[0][k], K[1][k] (NTT form), the two
-// Montgomery products written to blocks 0 and 1.
-__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd_key(uint32_t* __restrict__ Y,
-                                                                       const uint32_t* __restrict__ K, int krows,
-                                                                       int r, int logN,
-                                                                       const uint32_t* __restrict__ tw,
-                                                                       const uint32_t* __restrict__ twp,
-                                                                       const uint32_t* __restrict__ qtab,
-                                                                       const uint32_t* __restrict__ qinv) {
-  __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
-  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
-  const int N = 1 << logN;
-  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
-  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
-  const int c = blockIdx.x * kRowsPerCta + sub;
-  const size_t coff = (size_t)c * kRowLen;
-  uint32_t* a = Y + ((size_t)b * 2 * r + p) * N + coff;
-  uint32_t x[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
-  rows_fwd_core(x, c, j0, s + sub * (kRowLen + kRowLen / 16), N, tw + (size_t)p * N, twp + (size_t)p * N, q);
-  const uint4* kb = reinterpret_cast<const uint4*>(K + (size_t)p * N + coff + 16 * j0);
-  const uint4* ka = reinterpret_cast<const uint4*>(K + (size_t)(krows + p) * N + coff + 16 * j0);
-  uint4* o0 = reinterpret_cast<uint4*>(a + 16 * j0);
-  uint4* o1 = reinterpret_cast<uint4*>(Y + ((size_t)b * 2 * r + r + p) * N + coff + 16 * j0);
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const uint4 vb = __ldg(kb + v), va = __ldg(ka + v);
-    o0[v] = make_uint4(mont_mul(x[4 * v], vb.x, q, qi), mont_mul(x[4 * v + 1], vb.y, q, qi),
-                       mont_mul(x[4 * v + 2], vb.z, q, qi), mont_mul(x[4 * v + 3], vb.w, q, qi));
-    o1[v] = make_uint4(mont_mul(x[4 * v], va.x, q, qi), mont_mul(x[4 * v + 1], va.y, q, qi),
-                       mont_mul(x[4 * v + 2], va.z, q, qi), mont_mul(x[4 * v + 3], va.w, q, qi));
-  }
-}
-
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __restrict__ data, RowMap rm, int r,
                                                                    int logN, const uint32_t* __restrict__ tw,
                                                                    const uint32_t* __restrict__ twp,
@@ -411,6 +321,193 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __r
   for (int k = 0; k < 16; ++k) a[j0 + 16 * k] = x[k];
 }
 
+// ------------------------------------------------ fused transform-domain pass
+// A ring product's forward row stages, its pointwise products and the inverse
+// row stages of the results all work on the same 256-word matrix rows, so one
+// kernel runs them back to back on registers: the products never go to
+// memory in transform form.  16 threads per matrix row as in the row passes;
+// a thread holds the same positions of every operand, so each twiddle pair is
+// loaded once for all of them.  Exchange slots: one padded row per operand.
+constexpr int kSlot = kRowLen + kRowLen / 16;
+
+template <int R>
+__device__ __forceinline__ void rows_fwd_multi(uint32_t (&x)[R][16], int c, int j0, uint32_t* sr, int N,
+                                               const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                               uint32_t q) {
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const int m = N / (32 * h);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = c * (8 / h) + k / (2 * h);
+      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+#pragma unroll
+      for (int o = 0; o < R; ++o) ct_bfly(x[o][k], x[o][k + h], tw, twp, q);
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < R; ++o)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sr[o * kSlot + rpad(j0 + 16 * k)] = x[o][k];
+  __syncwarp();
+#pragma unroll
+  for (int o = 0; o < R; ++o)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[o][j] = sr[o * kSlot + rpad(16 * j0 + j)];
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const int m = N / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
+      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+#pragma unroll
+      for (int o = 0; o < R; ++o) ct_bfly(x[o][j], x[o][j + h], tw, twp, q);
+    }
+  }
+}
+
+// Inverse row stages: x[o][j] = row[16 j0 + j] in [0, 2q) on entry; on exit
+// x[o][k] = row[j0 + 16 k], in [0, 2q), ready for the column stages.
+template <int R>
+__device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int j0, uint32_t* sr, int N,
+                                               const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                               uint32_t q) {
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1) {
+    const int m = N / (2 * h);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
+      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+#pragma unroll
+      for (int o = 0; o < R; ++o) gs_bfly(x[o][j], x[o][j + h], tw, twp, q);
+    }
+  }
+  __syncwarp();  // the forward exchange reads of this row are done
+#pragma unroll
+  for (int o = 0; o < R; ++o)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sr[o * kSlot + rpad(16 * j0 + j)] = x[o][j];
+  __syncwarp();
+#pragma unroll
+  for (int o = 0; o < R; ++o)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[o][k] = sr[o * kSlot + rpad(j0 + 16 * k)];
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1) {
+    const int m = N / (32 * h);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const int i = c * (8 / h) + k / (2 * h);
+      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+#pragma unroll
+      for (int o = 0; o < R; ++o) gs_bfly(x[o][k], x[o][k + h], tw, twp, q);
+    }
+  }
+}
+
+// Karatsuba tensor product (Sec. 5 "Karatsuba Polynomial Multiplication") in
+// the transform domain: X = [batch][4][r][N] holds (B1, A1, B2, A2) after the
+// forward column stages; the kernel finishes their transforms, forms
+// D0 = B1 B2, D2 = A1 A2, D1 = (A1 + B1)(A2 + B2) - D0 - D2 (Montgomery
+// products) and runs the inverse row stages of D0, D1, D2 into blocks 0..2.
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
+                                                                      const uint32_t* __restrict__ tw,
+                                                                      const uint32_t* __restrict__ twp,
+                                                                      const uint32_t* __restrict__ itw,
+                                                                      const uint32_t* __restrict__ itwp,
+                                                                      const uint32_t* __restrict__ qtab,
+                                                                      const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 4 * kSlot];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const size_t rowN = (size_t)r * N;
+  const int c = blockIdx.x * kRowsPerCta + sub;
+  uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N + (size_t)c * kRowLen;
+  uint32_t* sr = s + sub * 4 * kSlot;
+  uint32_t x[4][16];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[o][k] = base[o * rowN + j0 + 16 * k];
+  rows_fwd_multi<4>(x, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t B1 = reduce4(x[0][j], q), A1 = reduce4(x[1][j], q);
+    const uint32_t B2 = reduce4(x[2][j], q), A2 = reduce4(x[3][j], q);
+    const uint32_t d0 = mont_mul(B1, B2, q, qi), d2 = mont_mul(A1, A2, q, qi);
+    const uint32_t t = mont_mul(add_mod(A1, B1, q), add_mod(A2, B2, q), q, qi);
+    x[0][j] = d0;
+    x[1][j] = sub_mod(sub_mod(t, d0, q), d2, q);
+    x[2][j] = d2;
+  }
+  uint32_t (&y)[3][16] = *reinterpret_cast<uint32_t (*)[3][16]>(&x[0][0]);
+  rows_inv_multi<3>(y, c, j0, sr, N, itw + (size_t)p * N, itwp + (size_t)p * N, q);
+#pragma unroll
+  for (int o = 0; o < 3; ++o)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) base[o * rowN + j0 + 16 * k] = y[o][k];
+}
+
+// Key product of a key switch (Sec. 6): Y = [batch][2][r][N] holds the lifted
+// polynomial in block 0 after the forward column stages; the kernel finishes
+// its transform, multiplies it by the key rows K[0][p], K[1][p] (transform
+// form, Montgomery) and runs the inverse row stages of both products into
+// blocks 0 and 1.
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __restrict__ Y,
+                                                                   const uint32_t* __restrict__ K, int krows, int r,
+                                                                   int logN, const uint32_t* __restrict__ tw,
+                                                                   const uint32_t* __restrict__ twp,
+                                                                   const uint32_t* __restrict__ itw,
+                                                                   const uint32_t* __restrict__ itwp,
+                                                                   const uint32_t* __restrict__ qtab,
+                                                                   const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const int c = blockIdx.x * kRowsPerCta + sub;
+  const size_t coff = (size_t)c * kRowLen;
+  uint32_t* y0 = Y + ((size_t)b * 2 * r + p) * N + coff;
+  uint32_t* y1 = y0 + (size_t)r * N;
+  uint32_t* sr = s + sub * 2 * kSlot;
+  uint32_t x[2][16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[0][k] = y0[j0 + 16 * k];
+  {
+    uint32_t (&x0)[1][16] = *reinterpret_cast<uint32_t (*)[1][16]>(&x[0][0]);
+    rows_fwd_multi<1>(x0, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+  }
+  // Montgomery products accept one operand in [0, 4q): 4 q^2 < q 2^32
+  const uint4* kb = reinterpret_cast<const uint4*>(K + (size_t)p * N + coff + 16 * j0);
+  const uint4* ka = reinterpret_cast<const uint4*>(K + (size_t)(krows + p) * N + coff + 16 * j0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 vb = __ldg(kb + v), va = __ldg(ka + v);
+    const uint32_t kbv[4] = {vb.x, vb.y, vb.z, vb.w}, kav[4] = {va.x, va.y, va.z, va.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t d = x[0][4 * v + u];
+      x[0][4 * v + u] = mont_mul(d, kbv[u], q, qi);
+      x[1][4 * v + u] = mont_mul(d, kav[u], q, qi);
+    }
+  }
+  rows_inv_multi<2>(x, c, j0, sr, N, itw + (size_t)p * N, itwp + (size_t)p * N, q);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    y0[j0 + 16 * k] = x[0][k];
+    y1[j0 + 16 * k] = x[1][k];
+  }
+}
+
 static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
                      cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
@@ -460,39 +557,68 @@ static void cols_fwd_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int r
 #undef FHE_NTT_COLS_F
 }
 
-// Forward transforms of X = [nbatch][4][r][N] and the Karatsuba products,
-// leaving D0, D1, D2 in blocks 0..2 (the row pass carries the products).
-int launch_ntt_fwd_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st) {
+static void cols_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
+                        cudaStream_t st) {
+  const int logN = ctx->prm.logN, logN1 = logN - 8;
+  dim3 g(kRowLen / 32, rows);
+#define FHE_NTT_COLS_ONLY(L)                                                                                 \
+  case L:                                                                                                    \
+    if (inverse)                                                                                             \
+      k_ntt_cols_inv<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->d_q,      \
+                                              ctx->d_nscale, ctx->d_nscale_sh);                              \
+    else                                                                                                     \
+      k_ntt_cols_fwd<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q);       \
+    break;
+  switch (logN1) { FHE_NTT_COLS_ONLY(5) FHE_NTT_COLS_ONLY(6) FHE_NTT_COLS_ONLY(7) FHE_NTT_COLS_ONLY(8) }
+#undef FHE_NTT_COLS_ONLY
+}
+
+int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
-  if (logN <= 12 || (size_t)nbatch * 4 * r > 65535u || (size_t)nbatch * r > 65535u) {
+  if (logN <= 12 || (size_t)nbatch * 4 * r > 65535u) {
     int rc = launch_ntt(ctx, X, nbatch * 4, r, r, r, false, st);
-    return rc ? rc : launch_pointwise_tensor(ctx, X, r, nbatch, st);
+    if (!rc) rc = launch_pointwise_tensor(ctx, X, r, nbatch, st);
+    return rc ? rc : launch_ntt(ctx, X, nbatch, 3 * r, 4 * r, r, true, st);
   }
   {
-    ProfScope ps(ctx, FHE_K_NTT_FWD, 2, st);
-    cols_fwd_launch(ctx, X, RowMap{r, r}, nbatch * 4 * r, r, st);
-    dim3 grid((N >> 8) / kKaraRows, nbatch * r);
-    k_ntt_rows_fwd_kara<<<grid, 64 * kKaraRows, 0, st>>>(X, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q,
-                                                          ctx->d_qinv);
+    ProfScope ps(ctx, FHE_K_NTT_FWD, 1, st);
+    cols_launch(ctx, X, RowMap{r, r}, nbatch * 4 * r, r, false, st);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
+    dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
+    k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_ipsi,
+                                                         ctx->d_ipsi_sh, ctx->d_q, ctx->d_qinv);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);
+    cols_launch(ctx, X, RowMap{3 * r, 4 * r}, nbatch * 3 * r, r, true, st);
   }
   return FHE_OK;
 }
 
-// Forward transform of block 0 of Y = [nbatch][2][r][N] and its products with
-// the key K = [2][krows][N] (NTT form) into blocks 0 and 1.
-int launch_ntt_fwd_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
-                       cudaStream_t st) {
+int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
+                    cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
-  if (logN <= 12 || (size_t)nbatch * r > 65535u) {
+  if (r > krows) return FHE_EINVAL;
+  if (logN <= 12 || (size_t)nbatch * 2 * r > 65535u) {
     int rc = launch_ntt(ctx, Y, nbatch, r, 2 * r, r, false, st);
-    return rc ? rc : launch_pointwise_key(ctx, Y, K, krows, r, nbatch, st);
+    if (!rc) rc = launch_pointwise_key(ctx, Y, K, krows, r, nbatch, st);
+    return rc ? rc : launch_ntt(ctx, Y, nbatch * 2, r, r, r, true, st);
   }
   {
-    ProfScope ps(ctx, FHE_K_NTT_FWD, 2, st);
-    cols_fwd_launch(ctx, Y, RowMap{r, 2 * r}, nbatch * r, r, st);
+    ProfScope ps(ctx, FHE_K_NTT_FWD, 1, st);
+    cols_launch(ctx, Y, RowMap{r, 2 * r}, nbatch * r, r, false, st);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
     dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
-    k_ntt_rows_fwd_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q,
-                                                          ctx->d_qinv);
+    k_ntt_rows_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_ipsi,
+                                                      ctx->d_ipsi_sh, ctx->d_q, ctx->d_qinv);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);
+    cols_launch(ctx, Y, RowMap{r, r}, nbatch * 2 * r, r, true, st);
   }
   return FHE_OK;
 }

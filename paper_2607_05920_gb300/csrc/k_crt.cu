@@ -17,6 +17,8 @@
 //     subtracted (mod 2^(32 LB)), giving the two's complement of the signed
 //     exact product.
 //  4. epilogue on the thread's limb column (see Epi in common.cuh).
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime)
+
 #include "common.cuh"
 
 namespace fhe {
@@ -365,10 +367,11 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
 constexpr int kTcRows = 128;
 constexpr int kTcYWarps = 8;                // two threads per coefficient row
 constexpr int kTcEWarps = 8;                // two groups of four, alternating tiles
-constexpr int kTcWarpProd = kTcYWarps + kTcEWarps;  // residues and addends
+constexpr int kTcWarpProd = kTcYWarps + kTcEWarps;  // residues
 constexpr int kTcWarpMma = kTcWarpProd + 1;         // TMEM owner, MMA issue
 constexpr int kTcWarpProdB = kTcWarpMma + 1;        // B slices
-constexpr int kTcThreads = 32 * (kTcWarpProdB + 1);
+constexpr int kTcWarpProdAdd = kTcWarpProdB + 1;    // staged addends
+constexpr int kTcThreads = 32 * (kTcWarpProdAdd + 1);
 constexpr int kTcNX = 3;                    // residue stages
 constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficients
 constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
@@ -462,36 +465,56 @@ struct TcShape {
   int acc_cols, nacc;              // TMEM columns per accumulator, accumulators
   int nadd;                        // staged addend buffers (0: the epilogue reads the addend from global)
   int const_bytes;                 // shared bytes of the per-prime constants
+  int limb;                        // 1: a limb column per epilogue group (some tile drains TMEM first)
 };
 
 // Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
-// residue stages, two A stages (K 64), two B slices (K 32), one limb column
-// per epilogue group and the staged addend buffers.
-static size_t tc_smem_bytes(const TcShape& sh, int add_limbs) {
-  return (size_t)kTcHead + sh.const_bytes + kTcFsx + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage +
-         2 * (size_t)sh.MT * 16 * 64 + 2 * (size_t)sh.MT * 4 * kTcRows * 4 + (size_t)sh.nadd * add_limbs * 512;
+// residue stages, two A stages (K 64, or K 128 with B resident), B (two K 32
+// slices streamed per chunk, or all of it resident), one limb column per
+// epilogue group when some tile needs it, and the staged addend buffers.
+static size_t tc_b_bytes(const TcShape& sh, bool res) {
+  const int KS = (sh.r + 4) >> 2;
+  return (size_t)(res ? (KS + 1) / 2 : 2) * sh.MT * 16 * 64;
+}
+static size_t tc_smem_bytes(const TcShape& sh, int add_limbs, bool res) {
+  return (size_t)kTcHead + sh.const_bytes + kTcFsx + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage * (res ? 2 : 1) +
+         tc_b_bytes(sh, res) + (sh.limb ? 2 * (size_t)sh.MT * 4 * kTcRows * 4 : 0) + (size_t)sh.nadd * add_limbs * 512;
 }
 
+// RES: B (all 4(r + 1) digits of every output column) stays in shared memory
+// for the whole persistent kernel and an A chunk spans two residue chunks
+// (K 128), so the MMA thread polls one barrier per eight k-steps; each of its
+// barrier polls, MMAs and commits costs it 100-250 cycles, which otherwise
+// bounds the tile rate.  Used when B fits (the tensor-product shape).
+template <bool RES>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_crt_tc(const uint32_t* __restrict__ in, size_t in_pstride, size_t in_bstride, TcShape sh,
+    k_crt_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_xp,
+             const __grid_constant__ CUtensorMap tm_add, TcShape sh,
              uint32_t* __restrict__ out, size_t out_pstride, size_t out_bstride, EpiArgs epi, int N,
              const uint32_t* __restrict__ qtab, const uint2* __restrict__ cinv, const float* __restrict__ invq,
              const uint16_t* __restrict__ bmat, int pmax) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (smem_addr(smem) & 1023u) {  // TMA boxes and MMA operands assume 1 KB alignment
+    if (tid == 0) atomicOr(&g_fhe_dev_status, 2u);
+    return;
+  }
   const int r = sh.r, MT = sh.MT;
   const int P = 16 * MT;
   const int KS = (r + 4) >> 2;    // k-steps of 16 over the 4 (r + 1) digits
   const int nch = (KS + 3) >> 2;  // chunks of 4 k-steps (16 primes)
   const uint32_t bslice = (uint32_t)P * 64u;  // bytes of a K-32 slice of B
+  constexpr int CPA = RES ? 2 : 1;             // residue chunks per A chunk
+  constexpr uint32_t kAStage = (uint32_t)kTcAStage * CPA, kASbo = 1024u * CPA;
+  const int nchA = (nch + CPA - 1) / CPA;      // A chunks per tile
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   uint4* CONST = reinterpret_cast<uint4*>(smem + kTcHead);
   float* FSX = reinterpret_cast<float*>(smem + kTcHead + sh.const_bytes);
   uint8_t* X = smem + kTcHead + sh.const_bytes + kTcFsx;
   uint8_t* A = X + kTcNX * kTcXStage;
-  uint8_t* B = A + 2 * kTcAStage;
-  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + 2 * bslice);
-  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (size_t)2 * 4 * MT * kTcRows);
+  uint8_t* B = A + 2 * kAStage;
+  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + (size_t)(RES ? (KS + 1) / 2 : 2) * bslice);
+  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (sh.limb ? (size_t)2 * 4 * MT * kTcRows : 0));
   const uint32_t bar0 = smem_addr(smem);
   auto x_full = [&](int s) { return bar0 + 8u * s; };
   auto x_empty = [&](int s) { return bar0 + 8u * (3 + s); };
@@ -548,39 +571,53 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == kTcWarpProd) {
     if (lane == 0) {
-      // producer: per tile the addend limbs, per chunk the residue rows and two B slices
-      int g = 0, tl = 0;
+      // producer: one TMA box (128 coefficients x 16 primes) per chunk; at
+      // each tile start the next tile's residues are prefetched into L2
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x) {
+        int n0, poly, b;
+        tile_of(t, n0, poly, b);
+        if (t + (int)gridDim.x < sh.ntiles) {
+          int n0n, polyn, bn;
+          tile_of(t + gridDim.x, n0n, polyn, bn);
+          tma_prefetch_4d(&tm_xp, n0n, 0, polyn, bn);
+        }
+        for (int c = 0; c < nch && ok; ++c, ++g) {
+          const int sx = g % kTcNX;
+          if (g >= kTcNX && !(ok = mbar_wait(x_empty(sx), (uint32_t)((g / kTcNX) - 1) & 1u))) break;
+          mbar_expect_tx(x_full(sx), (uint32_t)kTcXStage);
+          tma_load_4d(smem_addr(X + sx * kTcXStage), &tm_x, n0, 16 * c, poly, b, x_full(sx));
+        }
+      }
+    }
+  } else if (warp == kTcWarpProdAdd) {
+    if (lane == 0 && sh.nadd) {
+      // addend limbs of each tile, nadd stages ahead of the epilogue
+      int tl = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
         int n0, poly, b;
         tile_of(t, n0, poly, b);
-        if (sh.nadd) {
-          const int s = tl % sh.nadd;
-          if (tl >= sh.nadd &&
-              !(ok = mbar_wait(add_empty((tl - sh.nadd) & 1), (uint32_t)((tl - sh.nadd) >> 1) & 1u)))
-            break;
-          const bool has = add_limbs > 0 && poly < epi.add_polys;
-          mbar_expect_tx(add_full(tl & 1), has ? (uint32_t)add_limbs * 512u : 0u);
-          if (has) {
-            const uint32_t* ad = epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0;
-            uint8_t* dst = ADD + (size_t)s * add_limbs * 512;
-            for (int l = 0; l < add_limbs; ++l)
-              bulk_g2s(smem_addr(dst + 512 * l), ad + (size_t)l * N, 512u, add_full(tl & 1));
-          }
-        }
-        const uint32_t* src = in + (size_t)b * in_bstride + (size_t)poly * in_pstride + n0;
-        for (int c = 0; c < nch && ok; ++c, ++g) {
-          const int sx = g % kTcNX;
-          if (g >= kTcNX && !(ok = mbar_wait(x_empty(sx), (uint32_t)((g / kTcNX) - 1) & 1u))) break;
-          const int rows = max(0, min(16, r - 16 * c));
-          mbar_expect_tx(x_full(sx), (uint32_t)rows * 512u);
-          for (int j = 0; j < rows; ++j)
-            bulk_g2s(smem_addr(X + sx * kTcXStage + 512 * j), src + (size_t)(16 * c + j) * N, 512u, x_full(sx));
-        }
+        const int s = tl % sh.nadd;
+        if (tl >= sh.nadd &&
+            !(ok = mbar_wait(add_empty((tl - sh.nadd) & 1), (uint32_t)((tl - sh.nadd) >> 1) & 1u)))
+          break;
+        const bool has = add_limbs > 0 && poly < epi.add_polys;
+        mbar_expect_tx(add_full(tl & 1), has ? (uint32_t)add_limbs * 512u : 0u);
+        if (has)
+          tma_load_4d(smem_addr(ADD + (size_t)s * add_limbs * 512), &tm_add, n0, 0, poly, b, add_full(tl & 1));
       }
     }
   } else if (warp == kTcWarpProdB) {
-    if (lane == 0) {
+    if (RES) {
+      if (lane == 0) {  // all of B once, on barrier b_full(0)
+        const int nsl = (KS + 1) / 2;
+        mbar_expect_tx(b_full(0), (uint32_t)nsl * bslice);
+        for (int c2 = 0; c2 < nsl; ++c2)
+          bulk_g2s(smem_addr(B + (size_t)c2 * bslice), bmat + (size_t)c2 * pmax * 32, bslice, b_full(0));
+      }
+    } else if (lane == 0) {
       // B slices (K 32 each, two per chunk), the same sequence for every tile
       int gb = 0;
       bool ok = true;
@@ -603,10 +640,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint64_t boff1 = (uint64_t)((2u * (uint32_t)mh * 512u) >> 4);
       const uint32_t idesc0 = (1u << 4) | ((16u * (uint32_t)mh >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
       const uint32_t idesc1 = (1u << 4) | ((16u * (uint32_t)(MT - mh) >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-      const uint64_t adesc0 = tc_desc(smem_addr(A), 128u, 1024u);
+      const uint64_t adesc0 = tc_desc(smem_addr(A), 128u, kASbo);
       const uint64_t bdesc0 = tc_desc(smem_addr(B), 128u, 512u);
       int g = 0, tl = 0;
       bool ok = true;
+      if (RES) ok = mbar_wait(b_full(0), 0u);
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
         const int ab = tl % sh.nacc;
         if (tl >= sh.nacc &&
@@ -614,26 +652,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(ab * sh.acc_cols);
-        for (int c = 0; c < nch && ok; ++c, ++g) {
-          const int s = g & 1;
-          if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
-          const uint64_t adesc = adesc0 + (uint64_t)((s * kTcAStage) >> 4);
-          const int nks = min(4, KS - 4 * c);
-          for (int h = 0; h < 2; ++h) {
-            const int gb = 2 * g + h, sb = gb & 1;
-            if (!(ok = mbar_wait(b_full(sb), (uint32_t)(gb >> 1) & 1u))) break;
-            const uint64_t bdesc = bdesc0 + (uint64_t)((sb * bslice) >> 4);
-            const int ke = min(nks, 2 * h + 2);
-            for (int ks = 2 * h; ks < ke; ++ks) {
+        if (RES) {
+          // B resident: k-step j of the tile reads slice j / 2 at 256 B (j odd)
+          uint64_t db = bdesc0;
+          for (int c = 0; c < nchA && ok; ++c, ++g) {
+            const int s = g & 1;
+            if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
+            const uint64_t adesc = adesc0 + (uint64_t)((s * kAStage) >> 4);
+            const int nks = min(8, KS - 8 * c);
+            for (int ks = 0; ks < nks; ++ks) {
               const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
-              const uint64_t da = adesc + (uint64_t)(16 * ks);            // + 256 B per k-step
-              const uint64_t db = bdesc + (uint64_t)(16 * (ks & 1));      // + 256 B per k-step
+              const uint64_t da = adesc + (uint64_t)(16 * ks);
               tc_mma(dbase, da, db, idesc0, accum);
               if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
+              db += (ks & 1) ? (uint64_t)((bslice - 256u) >> 4) : (uint64_t)16;
             }
-            tc_commit(b_empty(sb));
+            tc_commit(a_empty(s));
           }
-          tc_commit(a_empty(s));
+        } else {
+          for (int c = 0; c < nch && ok; ++c, ++g) {
+            const int s = g & 1;
+            if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
+            const uint64_t adesc = adesc0 + (uint64_t)((s * kAStage) >> 4);
+            const int nks = min(4, KS - 4 * c);
+            for (int h = 0; h < 2; ++h) {
+              const int gb = 2 * g + h, sb = gb & 1;
+              if (!(ok = mbar_wait(b_full(sb), (uint32_t)(gb >> 1) & 1u))) break;
+              const uint64_t bdesc = bdesc0 + (uint64_t)((sb * bslice) >> 4);
+              const int ke = min(nks, 2 * h + 2);
+              for (int ks = 2 * h; ks < ke; ++ks) {
+                const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t da = adesc + (uint64_t)(16 * ks);            // + 256 B per k-step
+                const uint64_t db = bdesc + (uint64_t)(16 * (ks & 1));      // + 256 B per k-step
+                tc_mma(dbase, da, db, idesc0, accum);
+                if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
+              }
+              tc_commit(b_empty(sb));
+            }
+            tc_commit(a_empty(s));
+          }
         }
         if (!ok) break;
         tc_commit(acc_full(tl & 1));
@@ -642,16 +699,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp < kTcYWarps) {
     // Y: digits of y_i (and kappa); thread (t, h) handles primes 8h .. 8h + 7 of every chunk of row t
     const int t0 = tid & (kTcRows - 1), h = tid >> 7;
-    int g = 0, tly = 0;
+    int g = 0, tly = 0, ga = 0;  // residue chunks, tiles, A chunks
     bool ok = true;
     for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tly) {
       float fs = 0.f;
       for (int c = 0; c < nch; ++c, ++g) {
-        const int sx = g % kTcNX, sa = g & 1;
+        const int sx = g % kTcNX, u = c % CPA, sa = ga & 1;
         if (!(ok = mbar_wait(x_full(sx), (uint32_t)(g / kTcNX) & 1u))) break;
-        if (g >= 2 && !(ok = mbar_wait(a_empty(sa), (uint32_t)((g >> 1) - 1) & 1u))) break;
+        if (u == 0 && ga >= 2 && !(ok = mbar_wait(a_empty(sa), (uint32_t)((ga >> 1) - 1) & 1u))) break;
         const uint32_t* xs = reinterpret_cast<const uint32_t*>(X + sx * kTcXStage) + 8 * h * kTcRows + t0;
-        uint8_t* arow = A + sa * kTcAStage + (t0 >> 3) * 1024 + (t0 & 7) * 16 + 4 * h * 128;
+        uint8_t* arow = A + sa * kAStage + (t0 >> 3) * kASbo + (t0 & 7) * 16 + (8 * u + 4 * h) * 128;
         const int i0 = 16 * c + 8 * h;
         uint32_t yv[8];
         if (16 * c + 16 <= r) {
@@ -697,8 +754,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           *reinterpret_cast<uint4*>(arow + jp * 128) = make_uint4(d[0], d[1], d[2], d[3]);
         }
         mbar_arrive(x_empty(sx));
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_arrive(a_full(sa));
+        if (u == CPA - 1 || c == nch - 1) {
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(a_full(sa));
+          ++ga;
+        }
       }
     }
   } else {
@@ -833,6 +893,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // Runs the tensor-core form when it applies; returns 1 if launched, 0 if the
 // caller must use the integer form (nothing enqueued).
+// Tensor maps for the TMA loads: 4-D u32 tensors [d3][d2][d1][d0] with element
+// strides s1, s2, s3 and a box of b0 x b1.  cuTensorMapEncodeTiled comes from
+// the driver through the runtime's entry-point query (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+static bool tmap_4d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, size_t s1,
+                    size_t s2, size_t s3, uint32_t b0, uint32_t b1) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || s1 == 0 || s2 == 0 || s3 == 0) return false;
+  const cuuint64_t dims[4] = {d0, d1, d2, d3};
+  const cuuint64_t strides[3] = {(cuuint64_t)s1 * 4, (cuuint64_t)s2 * 4, (cuuint64_t)s3 * 4};
+  const cuuint32_t box[4] = {b0, b1, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t ib, int r, int npoly, int nbatch,
                      uint32_t* out, size_t op, size_t ob, const EpiArgs& epi, int need, cudaStream_t st) {
   const int N = ctx->N;
@@ -853,26 +943,59 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   const bool stageable = add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
                          !(epi.add_bstride & 3) && !(N & 3);
+  // the epilogue streams straight from TMEM unless the accumulator is single or
+  // some polynomial takes the general epilogue (the kernel's own rule)
+  sh.limb = sh.nacc == 1;
+  for (int p = 0; p < npoly && !sh.limb; ++p) {
+    const bool has_add = epi.add && p < epi.add_polys;
+    const bool smallp = p == 0 ? epi.small != nullptr : (p == 1 ? epi.small1 != nullptr : false);
+    const bool streamed = (epi.kind == Epi::kStore && !has_add && !smallp) ||
+                          (epi.kind == Epi::kRelin && epi.shift > 0 && !smallp);
+    if (!streamed) sh.limb = 1;
+  }
+  constexpr size_t kSmemMax = 227 * 1024;
   sh.nadd = 0;
+  const bool res = tc_smem_bytes(sh, add_limbs, true) <= kSmemMax;
   if (stageable) {
     for (int na = 2; na >= 1 && !sh.nadd; --na) {
       sh.nadd = na;
-      if (tc_smem_bytes(sh, add_limbs) > 227 * 1024) sh.nadd = 0;
+      if (tc_smem_bytes(sh, add_limbs, res) > kSmemMax) sh.nadd = 0;
     }
   }
-  const size_t smem = tc_smem_bytes(sh, add_limbs);
-  if (smem > 227 * 1024) return 0;
+  // residues [nbatch][npoly][r][N]: boxes of 128 x 16 for the stages, 128 x r for the L2 prefetch.
+  // A zero stride over a dimension longer than one (a broadcast) has no tensor map: such
+  // calls take the integer form, and such addends are read from global memory.
+  auto stride_or = [](size_t s, uint64_t extent, size_t dflt) -> size_t { return s ? s : (extent == 1 ? dflt : 0); };
+  CUtensorMap tm_x, tm_xp, tm_add;
+  memset(&tm_add, 0, sizeof(tm_add));
+  const size_t ipx = stride_or(ip, npoly, (size_t)r * N);
+  const size_t ibx = stride_or(ib, nbatch, ipx * npoly);
+  if (!tmap_4d(&tm_x, in, N, r, npoly, nbatch, N, ipx, ibx, kTcRows, 16) ||
+      !tmap_4d(&tm_xp, in, N, r, npoly, nbatch, N, ipx, ibx, kTcRows, (uint32_t)(r < 256 ? r : 256)))
+    return 0;
+  if (sh.nadd) {
+    const int apolys = epi.add_polys < npoly ? epi.add_polys : npoly;
+    const size_t apx = stride_or(epi.add_pstride, apolys, (size_t)add_limbs * N);
+    const size_t abx = stride_or(epi.add_bstride, nbatch, apx * apolys);
+    if (add_limbs > 256 || apolys < 1 ||
+        !tmap_4d(&tm_add, epi.add, N, add_limbs, apolys, nbatch, N, apx, abx, kTcRows, (uint32_t)add_limbs))
+      sh.nadd = 0;
+  }
+  const size_t smem = tc_smem_bytes(sh, add_limbs, res);
+  if (smem > kSmemMax) return 0;
   static thread_local int configured_dev = -1, nsm = 0;
   if (configured_dev != ctx->device) {
-    cudaFuncSetAttribute(k_crt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_crt_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    cudaFuncSetAttribute(k_crt_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     configured_dev = ctx->device;
   }
   const int grid = sh.ntiles < nsm ? sh.ntiles : nsm;
   ProfScope ps(ctx, FHE_K_CRT, 1, st);
   const size_t off = (size_t)r * (r - 1) / 2;
-  k_crt_tc<<<grid, kTcThreads, smem, st>>>(in, ip, ib, sh, out, op, ob, epi, N, ctx->d_q, ctx->d_crt_inv + off,
-                                           ctx->d_invq, ctx->d_crt_tc + ctx->crt_tc_off[r], 16 * ctx->crt_tc_mt);
+  auto kern = res ? k_crt_tc<true> : k_crt_tc<false>;
+  kern<<<grid, kTcThreads, smem, st>>>(tm_x, tm_xp, tm_add, sh, out, op, ob, epi, N, ctx->d_q, ctx->d_crt_inv + off,
+                                       ctx->d_invq, ctx->d_crt_tc + ctx->crt_tc_off[r], 16 * ctx->crt_tc_mt);
   return 1;
 }
 

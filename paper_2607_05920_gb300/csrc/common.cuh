@@ -114,6 +114,7 @@ struct fhe_ctx {
   uint16_t* d_lift_tc = nullptr;
   uint64_t* d_lift_off = nullptr;
   std::vector<size_t> crt_tc_off;
+  std::vector<uint8_t> crt_tc_exact22;  // per r: every column sum is below 2^22 in magnitude
   int crt_tc_mt = 0;              // output byte columns covered, in 16s
   int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 1 Garner (Eq. garner_mrc),
                                   // 2 direct CRT on the integer pipe only

@@ -17,6 +17,8 @@
 //     subtracted (mod 2^(32 LB)), giving the two's complement of the signed
 //     exact product.
 //  4. epilogue on the thread's limb column (see Epi in common.cuh).
+#include <type_traits>
+
 #include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime)
 
 #include "common.cuh"
@@ -466,6 +468,7 @@ struct TcShape {
   int nadd;                        // staged addend buffers (0: the epilogue reads the addend from global)
   int const_bytes;                 // shared bytes of the per-prime constants
   int limb;                        // 1: a limb column per epilogue group (some tile drains TMEM first)
+  int exact22;                     // 1: every column sum is below 2^22 (fp32 -> int by one exact addition)
 };
 
 // Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
@@ -823,33 +826,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
         have_add_stage = true;
       }
+      // limbs below the relinearisation's rounding bit only feed the carry
+      const int lfirst = mode == 2 ? min(rs.rl, rs.sl) : 0;
       long long carry = 0;
-      for (int m = 0; m < MT; ++m) {
-        uint32_t v[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(base + 16u * (uint32_t)m));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      // column sums (exact integers in fp32) -> 32-bit limbs: limb l = sum_u S_{4l+u} 256^u + carry.
+      // With |S| < 2^22 the low mantissa bits of S + 1.5 2^23 are S (one FADD), else cvt.rni.
+      auto drain = [&](auto exact) {
+        for (int m = 0; m < MT; ++m) {
+          uint32_t v[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(base + 16u * (uint32_t)m));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          int sv[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long val = carry + (long long)__float2int_rn(__uint_as_float(v[4 * q])) +
-                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 1])) * 256LL +
-                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 2])) * 65536LL +
-                                (long long)__float2int_rn(__uint_as_float(v[4 * q + 3])) * 16777216LL;
-          carry = val >> 32;
-          const int l = 4 * m + q;
-          const uint32_t x = (uint32_t)val;
-          if (!direct) {
-            limb[(size_t)l * kTcRows] = x;
-          } else if (mode == 1) {
-            if (l < epi.out_limbs) dst[(size_t)l * N] = l < nlo ? (x & limb_mask(l, ob)) : 0u;
-          } else {
-            rs.push_x(l, x);
+          for (int u = 0; u < 16; ++u)
+            sv[u] = decltype(exact)::value ? __float_as_int(__uint_as_float(v[u]) + 12582912.0f) - 0x4B400000
+                                           : __float2int_rn(__uint_as_float(v[u]));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const long long val = carry + (long long)sv[4 * q] + (long long)sv[4 * q + 1] * 256LL +
+                                  (long long)sv[4 * q + 2] * 65536LL + (long long)sv[4 * q + 3] * 16777216LL;
+            carry = val >> 32;
+            const int l = 4 * m + q;
+            const uint32_t x = (uint32_t)val;
+            if (!direct) {
+              if (l >= lfirst) limb[(size_t)l * kTcRows] = x;
+            } else if (mode == 1) {
+              if (l < epi.out_limbs) dst[(size_t)l * N] = l < nlo ? (x & limb_mask(l, ob)) : 0u;
+            } else {
+              rs.push_x(l, x);
+            }
           }
         }
-      }
+      };
+      if (sh.exact22)
+        drain(std::true_type{});
+      else
+        drain(std::false_type{});
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       mbar_arrive(acc_empty(eg));
       if (sh.nadd && !have_add_stage && !(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
@@ -865,7 +881,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (l0 + q < epi.out_limbs) dst[(size_t)(l0 + q) * N] = xv[q] & limb_mask(l0 + q, ob);
         }
       } else if (mode == 2) {
-        for (int l0 = 0; l0 < 4 * MT; l0 += 8) {
+        for (int l0 = lfirst; l0 < 4 * MT; l0 += 8) {
           uint32_t xv[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) xv[q] = (l0 + q < 4 * MT) ? limb[(size_t)(l0 + q) * kTcRows] : 0u;
@@ -940,6 +956,7 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
   while (sh.acc_cols < 16 * MT) sh.acc_cols <<= 1;
   sh.nacc = 2 * sh.acc_cols <= 512 ? 2 : 1;
   sh.const_bytes = (r * 16 + 1023) & ~1023;
+  sh.exact22 = ctx->crt_tc_exact22.size() > (size_t)r ? ctx->crt_tc_exact22[r] : 0;
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   const bool stageable = add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
                          !(epi.add_bstride & 3) && !(N & 3);

@@ -223,6 +223,7 @@ static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const s
   const int P = 16 * MT;
   ctx->crt_tc_mt = MT;
   ctx->crt_tc_off.assign(R + 1, 0);
+  ctx->crt_tc_exact22.assign(R + 1, 0);
   size_t total = 0;
   for (int r = 1; r <= R; ++r) {
     ctx->crt_tc_off[r] = total;
@@ -236,6 +237,20 @@ static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const s
     const size_t off = (size_t)r * (r - 1) / 2;
     for (int i = 0; i < r; ++i) balanced_bytes(&qhat[(off + i) * kMaxLimbs], &dig[(size_t)i * 4 * kMaxLimbs]);
     balanced_bytes(&negm[(size_t)r * kMaxLimbs], &dig[(size_t)r * 4 * kMaxLimbs]);
+    // largest possible |S_p| over the columns: digits of y_i (< q < 2^30) are at
+    // most 128 in magnitude (64 for the top one), kappa's single digit at most r
+    int64_t smax = 0;
+    for (int p = 0; p < P; ++p) {
+      int64_t sp = 0;
+      for (int i = 0; i <= r; ++i)
+        for (int a = 0; a < 4 && a <= p; ++a) {
+          const int64_t c = dig[(size_t)i * 4 * kMaxLimbs + p - a];
+          const int64_t dm = i == r ? (a == 0 ? r : 0) : (a < 3 ? 128 : 64);
+          sp += dm * (c < 0 ? -c : c);
+        }
+      smax = sp > smax ? sp : smax;
+    }
+    ctx->crt_tc_exact22[r] = smax < ((int64_t)1 << 22) ? 1 : 0;
     const int nch = (r + 16) / 16;
     uint16_t* base = mat.data() + ctx->crt_tc_off[r];
     for (int c = 0; c < nch; ++c)

@@ -86,10 +86,9 @@ struct fhe_ctx {
   // device tables (Sec. 5 "Precomputation")
   uint32_t* d_q = nullptr;        // [R]
   uint32_t* d_qinv = nullptr;     // [R]  q^-1 mod 2^32 (Montgomery)
-  uint32_t* d_psi = nullptr;      // [R][N] psi^brv(k), forward twiddles (bit-reversed order)
-  uint32_t* d_psi_sh = nullptr;   // [R][N] Shoup companions floor(w 2^32 / q)
-  uint32_t* d_ipsi = nullptr;     // [R][N] psi^-brv(k)
-  uint32_t* d_ipsi_sh = nullptr;  // [R][N]
+  uint2* d_psi2 = nullptr;        // [R][N] (psi^brv(k), floor(w 2^32 / q)): forward twiddles (bit-reversed
+                                  // order) with their Shoup companions, one 64-bit load per butterfly
+  uint2* d_ipsi2 = nullptr;       // [R][N] (psi^-brv(k), Shoup companion)
   uint32_t* d_nscale = nullptr;   // [R]  N^-1 * 2^32 mod q (INTT scale, undoes one Montgomery factor)
   uint32_t* d_nscale_sh = nullptr;// [R]
   uint32_t* d_pow2 = nullptr;     // [R][kMaxLiftLimbs] 2^(32 l) mod q

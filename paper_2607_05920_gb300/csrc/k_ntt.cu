@@ -29,7 +29,7 @@ constexpr int kRowLen = 256;   // N2
 // x, y in [0, 2q) -> [0, 2q).  Shoup products with a lazy result in [0, 2q).
 __device__ __forceinline__ void ct_bfly(uint32_t& x, uint32_t& y, uint32_t w, uint32_t wp, uint32_t q) {
   const uint32_t q2 = 2u * q;
-  const uint32_t u = x >= q2 ? x - q2 : x;          // [0, 2q)
+  const uint32_t u = min(x, x - q2);                // [0, 2q): x - 2q wraps above x when x < 2q
   const uint32_t t = shoup_mul_lazy(y, w, wp, q);   // [0, 2q)
   x = u + t;                                        // [0, 4q)
   y = u - t + q2;                                   // (0, 4q)
@@ -38,13 +38,13 @@ __device__ __forceinline__ void gs_bfly(uint32_t& x, uint32_t& y, uint32_t w, ui
   const uint32_t q2 = 2u * q;
   const uint32_t s = x + y;                         // [0, 4q)
   const uint32_t d = x - y + q2;                    // (0, 4q)
-  x = s >= q2 ? s - q2 : s;                         // [0, 2q)
+  x = min(s, s - q2);                               // [0, 2q)
   y = shoup_mul_lazy(d, w, wp, q);                  // [0, 2q)
 }
 // [0, 4q) -> [0, q)
 __device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t q) {
-  x = x >= 2u * q ? x - 2u * q : x;
-  return x >= q ? x - q : x;
+  x = min(x, x - 2u * q);
+  return min(x, x - q);
 }
 
 // ---------------------------------------------------------------- one CTA
@@ -58,7 +58,7 @@ struct RowMap {
 
 template <bool INV>
 __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
-                                                   const uint32_t* __restrict__ tw, const uint32_t* __restrict__ twp,
+                                                   const uint2* __restrict__ tw,
                                                    const uint32_t* __restrict__ qtab,
                                                    const uint32_t* __restrict__ nscale,
                                                    const uint32_t* __restrict__ nscale_sh) {
@@ -66,8 +66,7 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
   const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.x, r);
   const uint32_t q = __ldg(qtab + p);
-  const uint32_t* w = tw + (size_t)p * N;
-  const uint32_t* wp = twp + (size_t)p * N;
+  const uint2* w = tw + (size_t)p * N;
   uint32_t* a = data + rm.row_of(blockIdx.x) * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = a[j];
   __syncthreads();
@@ -77,7 +76,8 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
       for (int b = threadIdx.x; b < half; b += blockDim.x) {
         const int i = b >> lt;
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
-        ct_bfly(s[j], s[j + (1 << lt)], __ldg(w + m + i), __ldg(wp + m + i), q);
+        const uint2 t2 = __ldg(w + m + i);
+        ct_bfly(s[j], s[j + (1 << lt)], t2.x, t2.y, q);
       }
       __syncthreads();
     }
@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
       for (int b = threadIdx.x; b < half; b += blockDim.x) {
         const int i = b >> lt;
         const int j = (i << (lt + 1)) + (b & ((1 << lt) - 1));
-        gs_bfly(s[j], s[j + (1 << lt)], __ldg(w + h + i), __ldg(wp + h + i), q);
+        const uint2 t2 = __ldg(w + h + i);
+        gs_bfly(s[j], s[j + (1 << lt)], t2.x, t2.y, q);
       }
       __syncthreads();
     }
@@ -109,8 +110,7 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
 // row, so twiddle loads are warp-wide broadcasts.
 template <int LOGN1>
 __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
-                                                             const uint32_t* __restrict__ tw,
-                                                             const uint32_t* __restrict__ twp,
+                                                             const uint2* __restrict__ tw,
                                                              const uint32_t* __restrict__ qtab) {
   constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
   __shared__ uint32_t s[N1 * 32];
@@ -118,8 +118,7 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restric
   const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.y, r);
   const uint32_t q = __ldg(qtab + p);
-  const uint32_t* w = tw + (size_t)p * N;
-  const uint32_t* wp = twp + (size_t)p * N;
+  const uint2* w = tw + (size_t)p * N;
   uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
   uint32_t x[16];
 #pragma unroll
@@ -131,7 +130,8 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restric
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = k / (2 * h);
-      ct_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      ct_bfly(x[k], x[k + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restric
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = j0 * (8 / h) + j / (2 * h);
-      ct_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      ct_bfly(x[j], x[j + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -156,8 +157,7 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restric
 
 template <int LOGN1>
 __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
-                                                             const uint32_t* __restrict__ tw,
-                                                             const uint32_t* __restrict__ twp,
+                                                             const uint2* __restrict__ tw,
                                                              const uint32_t* __restrict__ qtab,
                                                              const uint32_t* __restrict__ nscale,
                                                              const uint32_t* __restrict__ nscale_sh) {
@@ -167,8 +167,7 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restric
   const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.y, r);
   const uint32_t q = __ldg(qtab + p);
-  const uint32_t* w = tw + (size_t)p * N;
-  const uint32_t* wp = twp + (size_t)p * N;
+  const uint2* w = tw + (size_t)p * N;
   uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
   uint32_t x[16];
 #pragma unroll
@@ -180,7 +179,8 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restric
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = j0 * (8 / h) + j / (2 * h);
-      gs_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      gs_bfly(x[j], x[j + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restric
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = k / (2 * h);
-      gs_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      gs_bfly(x[k], x[k + h], t2.x, t2.y, q);
     }
   }
   const uint32_t sc = __ldg(nscale + p), scp = __ldg(nscale_sh + p);
@@ -215,7 +216,7 @@ __device__ __forceinline__ int rpad(int pos) { return pos + (pos >> 4); }
 // on entry; on exit x[j] = row[16 j0 + j] of the transform, reduced to [0, q).
 // sr: the row's padded shared-memory slot; the 16 threads are half a warp.
 __device__ __forceinline__ void rows_fwd_core(uint32_t (&x)[16], int c, int j0, uint32_t* sr, int N,
-                                              const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                              const uint2* __restrict__ w,
                                               uint32_t q) {
   // layout A: distance t = 16 h, stage index N/(2t), group c (8/h) + k/(2h)
 #pragma unroll
@@ -225,7 +226,8 @@ __device__ __forceinline__ void rows_fwd_core(uint32_t (&x)[16], int c, int j0, 
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = c * (8 / h) + k / (2 * h);
-      ct_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      ct_bfly(x[k], x[k + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -241,7 +243,8 @@ __device__ __forceinline__ void rows_fwd_core(uint32_t (&x)[16], int c, int j0, 
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
-      ct_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      ct_bfly(x[j], x[j + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -249,8 +252,7 @@ __device__ __forceinline__ void rows_fwd_core(uint32_t (&x)[16], int c, int j0, 
 }
 
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __restrict__ data, RowMap rm, int r,
-                                                                   int logN, const uint32_t* __restrict__ tw,
-                                                                   const uint32_t* __restrict__ twp,
+                                                                   int logN, const uint2* __restrict__ tw,
                                                                    const uint32_t* __restrict__ qtab) {
   __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
@@ -262,23 +264,21 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_fwd(uint32_t* __r
   uint32_t x[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) x[k] = a[j0 + 16 * k];
-  rows_fwd_core(x, c, j0, s + sub * (kRowLen + kRowLen / 16), N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+  rows_fwd_core(x, c, j0, s + sub * (kRowLen + kRowLen / 16), N, tw + (size_t)p * N, q);
   uint4* a4 = reinterpret_cast<uint4*>(a + 16 * j0);
 #pragma unroll
   for (int v = 0; v < 4; ++v) a4[v] = make_uint4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
 }
 
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __restrict__ data, RowMap rm, int r,
-                                                                   int logN, const uint32_t* __restrict__ tw,
-                                                                   const uint32_t* __restrict__ twp,
+                                                                   int logN, const uint2* __restrict__ tw,
                                                                    const uint32_t* __restrict__ qtab) {
   __shared__ uint32_t s[kRowsPerCta * (kRowLen + kRowLen / 16)];
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.y, r);
   const uint32_t q = __ldg(qtab + p);
-  const uint32_t* w = tw + (size_t)p * N;
-  const uint32_t* wp = twp + (size_t)p * N;
+  const uint2* w = tw + (size_t)p * N;
   const int c = blockIdx.x * kRowsPerCta + sub;
   uint32_t* a = data + rm.row_of(blockIdx.y) * N + (size_t)c * kRowLen;
   uint32_t* sr = s + sub * (kRowLen + kRowLen / 16);
@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __r
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
-      gs_bfly(x[j], x[j + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      gs_bfly(x[j], x[j + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_inv(uint32_t* __r
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = c * (8 / h) + k / (2 * h);
-      gs_bfly(x[k], x[k + h], __ldg(w + m + i), __ldg(wp + m + i), q);
+      const uint2 t2 = __ldg(w + m + i);
+      gs_bfly(x[k], x[k + h], t2.x, t2.y, q);
     }
   }
 #pragma unroll
@@ -332,7 +334,7 @@ constexpr int kSlot = kRowLen + kRowLen / 16;
 
 template <int R>
 __device__ __forceinline__ void rows_fwd_multi(uint32_t (&x)[R][16], int c, int j0, uint32_t* sr, int N,
-                                               const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                               const uint2* __restrict__ w,
                                                uint32_t q) {
 #pragma unroll
   for (int h = 8; h >= 1; h >>= 1) {
@@ -341,7 +343,8 @@ __device__ __forceinline__ void rows_fwd_multi(uint32_t (&x)[R][16], int c, int 
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = c * (8 / h) + k / (2 * h);
-      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+      const uint2 t2 = __ldg(w + m + i);
+      const uint32_t tw = t2.x, twp = t2.y;
 #pragma unroll
       for (int o = 0; o < R; ++o) ct_bfly(x[o][k], x[o][k + h], tw, twp, q);
     }
@@ -362,7 +365,8 @@ __device__ __forceinline__ void rows_fwd_multi(uint32_t (&x)[R][16], int c, int 
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
-      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+      const uint2 t2 = __ldg(w + m + i);
+      const uint32_t tw = t2.x, twp = t2.y;
 #pragma unroll
       for (int o = 0; o < R; ++o) ct_bfly(x[o][j], x[o][j + h], tw, twp, q);
     }
@@ -373,7 +377,7 @@ __device__ __forceinline__ void rows_fwd_multi(uint32_t (&x)[R][16], int c, int 
 // x[o][k] = row[j0 + 16 k], in [0, 2q), ready for the column stages.
 template <int R>
 __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int j0, uint32_t* sr, int N,
-                                               const uint32_t* __restrict__ w, const uint32_t* __restrict__ wp,
+                                               const uint2* __restrict__ w,
                                                uint32_t q) {
 #pragma unroll
   for (int h = 1; h <= 8; h <<= 1) {
@@ -382,7 +386,8 @@ __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int 
     for (int j = 0; j < 16; ++j) {
       if (j & h) continue;
       const int i = c * (128 / h) + j0 * (8 / h) + j / (2 * h);
-      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+      const uint2 t2 = __ldg(w + m + i);
+      const uint32_t tw = t2.x, twp = t2.y;
 #pragma unroll
       for (int o = 0; o < R; ++o) gs_bfly(x[o][j], x[o][j + h], tw, twp, q);
     }
@@ -404,7 +409,8 @@ __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int 
     for (int k = 0; k < 16; ++k) {
       if (k & h) continue;
       const int i = c * (8 / h) + k / (2 * h);
-      const uint32_t tw = __ldg(w + m + i), twp = __ldg(wp + m + i);
+      const uint2 t2 = __ldg(w + m + i);
+      const uint32_t tw = t2.x, twp = t2.y;
 #pragma unroll
       for (int o = 0; o < R; ++o) gs_bfly(x[o][k], x[o][k + h], tw, twp, q);
     }
@@ -417,10 +423,8 @@ __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int 
 // D0 = B1 B2, D2 = A1 A2, D1 = (A1 + B1)(A2 + B2) - D0 - D2 (Montgomery
 // products) and runs the inverse row stages of D0, D1, D2 into blocks 0..2.
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
-                                                                      const uint32_t* __restrict__ tw,
-                                                                      const uint32_t* __restrict__ twp,
-                                                                      const uint32_t* __restrict__ itw,
-                                                                      const uint32_t* __restrict__ itwp,
+                                                                      const uint2* __restrict__ tw,
+                                                                      const uint2* __restrict__ itw,
                                                                       const uint32_t* __restrict__ qtab,
                                                                       const uint32_t* __restrict__ qinv) {
   __shared__ uint32_t s[kRowsPerCta * 4 * kSlot];
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* 
   for (int o = 0; o < 4; ++o)
 #pragma unroll
     for (int k = 0; k < 16; ++k) x[o][k] = base[o * rowN + j0 + 16 * k];
-  rows_fwd_multi<4>(x, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+  rows_fwd_multi<4>(x, c, j0, sr, N, tw + (size_t)p * N, q);
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const uint32_t B1 = reduce4(x[0][j], q), A1 = reduce4(x[1][j], q);
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* 
     x[2][j] = d2;
   }
   uint32_t (&y)[3][16] = *reinterpret_cast<uint32_t (*)[3][16]>(&x[0][0]);
-  rows_inv_multi<3>(y, c, j0, sr, N, itw + (size_t)p * N, itwp + (size_t)p * N, q);
+  rows_inv_multi<3>(y, c, j0, sr, N, itw + (size_t)p * N, q);
 #pragma unroll
   for (int o = 0; o < 3; ++o)
 #pragma unroll
@@ -463,10 +467,8 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* 
 // blocks 0 and 1.
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __restrict__ Y,
                                                                    const uint32_t* __restrict__ K, int krows, int r,
-                                                                   int logN, const uint32_t* __restrict__ tw,
-                                                                   const uint32_t* __restrict__ twp,
-                                                                   const uint32_t* __restrict__ itw,
-                                                                   const uint32_t* __restrict__ itwp,
+                                                                   int logN, const uint2* __restrict__ tw,
+                                                                   const uint2* __restrict__ itw,
                                                                    const uint32_t* __restrict__ qtab,
                                                                    const uint32_t* __restrict__ qinv) {
   __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
   for (int k = 0; k < 16; ++k) x[0][k] = y0[j0 + 16 * k];
   {
     uint32_t (&x0)[1][16] = *reinterpret_cast<uint32_t (*)[1][16]>(&x[0][0]);
-    rows_fwd_multi<1>(x0, c, j0, sr, N, tw + (size_t)p * N, twp + (size_t)p * N, q);
+    rows_fwd_multi<1>(x0, c, j0, sr, N, tw + (size_t)p * N, q);
   }
   // Montgomery products accept one operand in [0, 4q): 4 q^2 < q 2^32
   const uint4* kb = reinterpret_cast<const uint4*>(K + (size_t)p * N + coff + 16 * j0);
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
       x[1][4 * v + u] = mont_mul(d, kav[u], q, qi);
     }
   }
-  rows_inv_multi<2>(x, c, j0, sr, N, itw + (size_t)p * N, itwp + (size_t)p * N, q);
+  rows_inv_multi<2>(x, c, j0, sr, N, itw + (size_t)p * N, q);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     y0[j0 + 16 * k] = x[0][k];
@@ -511,17 +513,16 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
 static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
                      cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
-  const uint32_t* tw = inverse ? ctx->d_ipsi : ctx->d_psi;
-  const uint32_t* twp = inverse ? ctx->d_ipsi_sh : ctx->d_psi_sh;
+  const uint2* tw = inverse ? ctx->d_ipsi2 : ctx->d_psi2;
   ProfScope ps(ctx, inverse ? FHE_K_NTT_INV : FHE_K_NTT_FWD, logN <= 12 ? 1 : 2, st);
   if (logN <= 12) {
     const int threads = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
     const size_t smem = (size_t)N * 4;
     if (inverse)
-      k_ntt_small<true><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, twp, ctx->d_q, ctx->d_nscale,
+      k_ntt_small<true><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,
                                                       ctx->d_nscale_sh);
     else
-      k_ntt_small<false><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, twp, ctx->d_q, ctx->d_nscale,
+      k_ntt_small<false><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,
                                                        ctx->d_nscale_sh);
     return FHE_OK;
   }
@@ -530,16 +531,16 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
 #define FHE_NTT_COLS(L)                                                                                    \
   case L:                                                                                                  \
     if (inverse)                                                                                           \
-      k_ntt_cols_inv<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q, ctx->d_nscale,     \
+      k_ntt_cols_inv<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,     \
                                                   ctx->d_nscale_sh);                                       \
     else                                                                                                   \
-      k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);                   \
+      k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, ctx->d_q);                   \
     break;
   if (!inverse) {
     switch (logN1) { FHE_NTT_COLS(5) FHE_NTT_COLS(6) FHE_NTT_COLS(7) FHE_NTT_COLS(8) }
-    k_ntt_rows_fwd<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);
+    k_ntt_rows_fwd<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, ctx->d_q);
   } else {
-    k_ntt_rows_inv<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, twp, ctx->d_q);
+    k_ntt_rows_inv<<<grows, 16 * kRowsPerCta, 0, st>>>(data, rm, r, logN, tw, ctx->d_q);
     switch (logN1) { FHE_NTT_COLS(5) FHE_NTT_COLS(6) FHE_NTT_COLS(7) FHE_NTT_COLS(8) }
   }
 #undef FHE_NTT_COLS
@@ -551,7 +552,7 @@ static void cols_fwd_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int r
   dim3 gcols(kRowLen / 32, rows);
 #define FHE_NTT_COLS_F(L)                                                                          \
   case L:                                                                                          \
-    k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q); \
+    k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi2, ctx->d_q); \
     break;
   switch (logN1) { FHE_NTT_COLS_F(5) FHE_NTT_COLS_F(6) FHE_NTT_COLS_F(7) FHE_NTT_COLS_F(8) }
 #undef FHE_NTT_COLS_F
@@ -564,10 +565,10 @@ static void cols_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows,
 #define FHE_NTT_COLS_ONLY(L)                                                                                 \
   case L:                                                                                                    \
     if (inverse)                                                                                             \
-      k_ntt_cols_inv<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_ipsi, ctx->d_ipsi_sh, ctx->d_q,      \
+      k_ntt_cols_inv<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_ipsi2, ctx->d_q,      \
                                               ctx->d_nscale, ctx->d_nscale_sh);                              \
     else                                                                                                     \
-      k_ntt_cols_fwd<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_q);       \
+      k_ntt_cols_fwd<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi2, ctx->d_q);       \
     break;
   switch (logN1) { FHE_NTT_COLS_ONLY(5) FHE_NTT_COLS_ONLY(6) FHE_NTT_COLS_ONLY(7) FHE_NTT_COLS_ONLY(8) }
 #undef FHE_NTT_COLS_ONLY
@@ -587,8 +588,8 @@ int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaS
   {
     ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
     dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
-    k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_ipsi,
-                                                         ctx->d_ipsi_sh, ctx->d_q, ctx->d_qinv);
+    k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi2, ctx->d_ipsi2,
+                                                         ctx->d_q, ctx->d_qinv);
   }
   {
     ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);
@@ -613,8 +614,8 @@ int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krow
   {
     ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
     dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
-    k_ntt_rows_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi, ctx->d_psi_sh, ctx->d_ipsi,
-                                                      ctx->d_ipsi_sh, ctx->d_q, ctx->d_qinv);
+    k_ntt_rows_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi2, ctx->d_ipsi2,
+                                                      ctx->d_q, ctx->d_qinv);
   }
   {
     ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);

@@ -188,6 +188,13 @@ static T* upload(fhe_ctx* ctx, const std::vector<T>& h) {
   return d;
 }
 
+// (value, Shoup companion) pairs, one 64-bit word per twiddle.
+static std::vector<uint2> interleave(const std::vector<uint32_t>& w, const std::vector<uint32_t>& wp) {
+  std::vector<uint2> out(w.size());
+  for (size_t i = 0; i < w.size(); ++i) out[i] = make_uint2(w[i], wp[i]);
+  return out;
+}
+
 // fp16 bit pattern of a small integer, |v| <= 2048 (exact).
 static uint16_t half_of_int(int v) {
   if (v == 0) return 0;
@@ -445,9 +452,8 @@ int build_tables(fhe_ctx* ctx) {
   if (!(ctx->d_crt_qhat = upload(ctx, qhat)) || !(ctx->d_crt_inv = upload(ctx, crt_inv)) ||
       !(ctx->d_crt_negm = upload(ctx, negm)) || !(ctx->d_invq = upload(ctx, invq)))
     return FHE_ENOMEM;
-  if (!(ctx->d_q = upload(ctx, q)) || !(ctx->d_qinv = upload(ctx, qinv)) || !(ctx->d_psi = upload(ctx, psi)) ||
-      !(ctx->d_psi_sh = upload(ctx, psi_sh)) || !(ctx->d_ipsi = upload(ctx, ipsi)) ||
-      !(ctx->d_ipsi_sh = upload(ctx, ipsi_sh)) || !(ctx->d_nscale = upload(ctx, nscale)) ||
+  if (!(ctx->d_q = upload(ctx, q)) || !(ctx->d_qinv = upload(ctx, qinv)) || !(ctx->d_psi2 = upload(ctx, interleave(psi, psi_sh))) ||
+      !(ctx->d_ipsi2 = upload(ctx, interleave(ipsi, ipsi_sh))) || !(ctx->d_nscale = upload(ctx, nscale)) ||
       !(ctx->d_nscale_sh = upload(ctx, nscale_sh)) || !(ctx->d_pow2 = upload(ctx, pow2)) || !(ctx->d_pow24 = upload(ctx, pow24)) ||
       !(ctx->d_red = upload(ctx, red)) || !(ctx->d_garner = upload(ctx, garner)) ||
       !(ctx->d_mprod = upload(ctx, mprod)))

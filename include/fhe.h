@@ -85,7 +85,8 @@ typedef struct {
   int32_t logP;   /* special modulus P = 2^logP of the switching keys                 */
   int32_t crt;    /* RNS -> limb reconstruction: FHE_CRT_DIRECT (0, default),
                      FHE_CRT_GARNER (1, the mixed-radix form of Sec. 2 Eq. garner_mrc)
-                     or FHE_CRT_DIRECT_INT (2); all give identical results          */
+                     FHE_CRT_DIRECT_INT (2) or FHE_CRT_DIRECT_CVT (3); all give
+                     identical results                                              */
   int32_t bgv_levels; /* BGV: top level L of the chain Q_l = q0 r^l (0 for CKKS)      */
   uint32_t t;         /* BGV: plaintext modulus, odd, 3 <= t < 2^31 (0 for CKKS)      */
   uint64_t bgv_q0;    /* BGV: odd, = 1 mod t                                         */
@@ -97,6 +98,9 @@ typedef struct {
                                 GEMM wherever r + 1 <= 255 and N is a multiple of 64      */
 #define FHE_CRT_GARNER 1     /* Garner's mixed-radix conversion, digits in the nested order   */
 #define FHE_CRT_DIRECT_INT 2 /* the direct CRT with its dense sum on the integer pipe only  */
+#define FHE_CRT_DIRECT_CVT 3 /* FHE_CRT_DIRECT with the column sums always converted by
+                                cvt.rni (FHE_CRT_DIRECT converts them with one exact fp32
+                                addition where a host-side bound shows |sum| < 2^22)      */
 
 typedef struct {
   uint32_t* data; /* device, uint32_t[cnum][2][L][N], L = ceil(logQ/32)               */

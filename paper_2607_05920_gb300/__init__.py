@@ -38,6 +38,7 @@ FHE_SCHEME_BGV = 1
 FHE_CRT_DIRECT = 0
 FHE_CRT_GARNER = 1
 FHE_CRT_DIRECT_INT = 2
+FHE_CRT_DIRECT_CVT = 3
 FHE_OP_MULT = 1
 FHE_OP_ROTATE = 2
 FHE_OP_ENCRYPT = 3

@@ -371,7 +371,8 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   if ((p->scheme != FHE_SCHEME_CKKS && p->scheme != FHE_SCHEME_BGV) || p->logN < 3 || p->logN > kMaxLogN ||
       p->logQ < 1 || p->logP < 1 ||
       p->logQ + p->logP > 32 * (kMaxLimbs - 3) || (alloc == nullptr) != (free_ == nullptr) ||
-      (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER && p->crt != FHE_CRT_DIRECT_INT)) {
+      (p->crt != FHE_CRT_DIRECT && p->crt != FHE_CRT_GARNER && p->crt != FHE_CRT_DIRECT_INT &&
+       p->crt != FHE_CRT_DIRECT_CVT)) {
     set_error("ctx_create: parameters out of range (logN %d, logQ %d, logP %d)", p->logN, p->logQ, p->logP);
     return FHE_EINVAL;
   }

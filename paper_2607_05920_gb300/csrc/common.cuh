@@ -115,7 +115,8 @@ struct fhe_ctx {
   std::vector<size_t> crt_tc_off;
   std::vector<uint8_t> crt_tc_exact22;  // per r: every column sum is below 2^22 in magnitude
   int crt_tc_mt = 0;              // output byte columns covered, in 16s
-  int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 1 Garner (Eq. garner_mrc),
+  int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 3 the same with cvt.rni
+                                  // conversion of the column sums, 1 Garner (Eq. garner_mrc),
                                   // 2 direct CRT on the integer pipe only
   // BGV (scheme FHE_SCHEME_BGV): chain constants per level, and bit lengths of Q_l
   fhe::BgvLevel* d_bgv_levels = nullptr;

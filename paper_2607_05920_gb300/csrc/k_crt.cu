@@ -956,7 +956,7 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
   while (sh.acc_cols < 16 * MT) sh.acc_cols <<= 1;
   sh.nacc = 2 * sh.acc_cols <= 512 ? 2 : 1;
   sh.const_bytes = (r * 16 + 1023) & ~1023;
-  sh.exact22 = ctx->crt_tc_exact22.size() > (size_t)r ? ctx->crt_tc_exact22[r] : 0;
+  sh.exact22 = ctx->crt_mode == FHE_CRT_DIRECT && ctx->crt_tc_exact22.size() > (size_t)r ? ctx->crt_tc_exact22[r] : 0;
   const int add_limbs = epi.add ? epi.add_limbs : 0;
   const bool stageable = add_limbs > 0 && !((uintptr_t)epi.add & 15) && !(epi.add_pstride & 3) &&
                          !(epi.add_bstride & 3) && !(N & 3);
@@ -1074,7 +1074,7 @@ int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, siz
     set_error("garner: %d limbs exceed %d", need, kMaxLimbs);
     return FHE_EINVAL;
   }
-  if (ctx->crt_mode == 0 &&
+  if ((ctx->crt_mode == FHE_CRT_DIRECT || ctx->crt_mode == FHE_CRT_DIRECT_CVT) &&
       tc_launch(ctx, in, in_pstride, in_bstride, r, npoly, nbatch, out, out_pstride, out_bstride, epi, need, st))
     return FHE_OK;
 #define FHE_GARNER_CASE(B)                                                                                       \

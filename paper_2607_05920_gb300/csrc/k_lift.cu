@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
 static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t sp, size_t sb, uint32_t* dst,
                           size_t dp, size_t db, int npoly, int nbatch, int r, cudaStream_t st) {
   const int N = ctx->N;
-  if (!ctx->d_lift_tc || ctx->crt_mode != 0 || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
+  if (!ctx->d_lift_tc || (ctx->crt_mode != FHE_CRT_DIRECT && ctx->crt_mode != FHE_CRT_DIRECT_CVT) || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
   LtShape sh;
   sh.r = r;
   sh.L = L;

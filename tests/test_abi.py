@@ -53,7 +53,7 @@ def test_ctx_create_rejects_bad_params_before_touching_the_device():
 
     h = ctypes.c_void_p()
     for prm in ((0, 2, 100, 100, 0), (0, 17, 100, 100, 0), (1, 11, 100, 100, 0), (0, 11, 0, 100, 0),
-                (0, 11, 3000, 3000, 0), (0, 11, 100, 100, 3)):
+                (0, 11, 3000, 3000, 0), (0, 11, 100, 100, 4), (0, 11, 100, 100, -1)):
         p = fhe.FheParams(*prm)
         rc = fhe.lib.fhe_ctx_create(ctypes.byref(p), fhe.ALLOC_FN(), fhe.FREE_FN(), None, ctypes.byref(h))
         assert rc == fhe.FHE_EINVAL

@@ -27,7 +27,7 @@ def _oracle_ct(limbs):
     return [tuple(bigint.from_limbs(limbs[c, p]) for p in range(2)) for c in range(limbs.shape[0])]
 
 
-@pytest.mark.parametrize("crt", [0, 1, 2], ids=["direct_tc", "garner", "direct_int"])
+@pytest.mark.parametrize("crt", [0, 1, 2, 3], ids=["direct_tc", "garner", "direct_int", "direct_tc_cvt"])
 @pytest.mark.parametrize("logN,La,Lb,logOut", [(11, 4, 4, 268), (11, 3, 1, 100), (8, 1, 1, 64), (14, 5, 7, 200),
                                                 (16, 2, 3, 64), (12, 40, 40, 2600)])
 def test_ring_mul_matches_exact_product(logN, La, Lb, logOut, crt):
@@ -51,7 +51,7 @@ def test_ring_mul_matches_exact_product(logN, La, Lb, logOut, crt):
     ctx.close()
 
 
-@pytest.mark.parametrize("crt", [0, 1, 2], ids=["direct_tc", "garner", "direct_int"])
+@pytest.mark.parametrize("crt", [0, 1, 2, 3], ids=["direct_tc", "garner", "direct_int", "direct_tc_cvt"])
 def test_ring_mul_every_limb_bucket(crt):
     """Outputs of 8 .. 128 limbs (every register bucket of the reconstruction), products wider than the output."""
     import paper_2607_05920_gb300 as fhe
@@ -71,7 +71,7 @@ def test_ring_mul_every_limb_bucket(crt):
     ctx.close()
 
 
-@pytest.fixture(scope="module", params=[0, 1, 2], ids=["direct_tc", "garner", "direct_int"])
+@pytest.fixture(scope="module", params=[0, 1, 2, 3], ids=["direct_tc", "garner", "direct_int", "direct_tc_cvt"])
 def c1(request):
     # N = 2^11, Q = P = 2^120 (the smallest workload), plus rotation keys; every reconstruction
     return make_pair(11, 120, 120, seed=11, rot_steps=(1, 3, -1, 1 << 10), crt=request.param)
@@ -161,7 +161,7 @@ def test_decoded_product_accuracy_c1(c1):
     assert np.abs(z - z1 * z2).max() <= 2.0 ** -10 * max(1.0, np.abs(z1 * z2).max())
 
 
-@pytest.mark.parametrize("crt", [0, 1, 2], ids=["direct_tc", "garner", "direct_int"])
+@pytest.mark.parametrize("crt", [0, 1, 2, 3], ids=["direct_tc", "garner", "direct_int", "direct_tc_cvt"])
 def test_two_pass_ring_mid_size(crt):
     """N = 2^14 (two-pass NTT), logQ = logP = 438, a batch of two: mult+relin+rescale and a rotation."""
     P = make_pair(14, 438, 438, seed=14, rot_steps=(5,), crt=crt)
@@ -192,7 +192,7 @@ def test_full_size_north_star_pair():
     assert got[0] == want
     P.ctx.close()
     # the Garner and integer-pipe reconstructions give the same ciphertext from the same keys
-    for mode in (fhe.FHE_CRT_GARNER, fhe.FHE_CRT_DIRECT_INT):
+    for mode in (fhe.FHE_CRT_GARNER, fhe.FHE_CRT_DIRECT_INT, fhe.FHE_CRT_DIRECT_CVT):
         Pg = make_pair(16, 1200, 1200, seed=16, crt=mode)
         assert ct_ints(Pg.ctx.mult_relin_rescale(ca, cb, 40))[0] == want
         Pg.ctx.close()
@@ -205,7 +205,7 @@ def test_full_size_batch_tensor_core_crt_equals_integer_crt():
     import torch
 
     outs = []
-    for mode in (fhe.FHE_CRT_DIRECT, fhe.FHE_CRT_DIRECT_INT):
+    for mode in (fhe.FHE_CRT_DIRECT, fhe.FHE_CRT_DIRECT_INT, fhe.FHE_CRT_DIRECT_CVT):
         P = make_pair(16, 1200, 1200, seed=17, crt=mode)
         g = fs.rng(170)
         la = random_ct_limbs(g, 8, P.prm.N, 1200)
@@ -214,3 +214,4 @@ def test_full_size_batch_tensor_core_crt_equals_integer_crt():
         outs.append(out.data.cpu())
         P.ctx.close()
     assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[2])

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restric
 }
 
 template <int LOGN1>
-__global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
                                                              const uint2* __restrict__ tw,
                                                              const uint32_t* __restrict__ qtab,
                                                              const uint32_t* __restrict__ nscale,
@@ -422,7 +422,7 @@ __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int 
 // forward column stages; the kernel finishes their transforms, forms
 // D0 = B1 B2, D2 = A1 A2, D1 = (A1 + B1)(A2 + B2) - D0 - D2 (Montgomery
 // products) and runs the inverse row stages of D0, D1, D2 into blocks 0..2.
-__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
+__global__ void __launch_bounds__(16 * kRowsPerCta, 5) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
                                                                       const uint2* __restrict__ tw,
                                                                       const uint2* __restrict__ itw,
                                                                       const uint32_t* __restrict__ qtab,

@@ -469,6 +469,7 @@ struct TcShape {
   int const_bytes;                 // shared bytes of the per-prime constants
   int limb;                        // 1: a limb column per epilogue group (some tile drains TMEM first)
   int exact22;                     // 1: every column sum is below 2^22 (fp32 -> int by one exact addition)
+  int lbase;                       // first limb a limb column holds (limbs below only feed the carry)
 };
 
 // Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
@@ -477,11 +478,12 @@ struct TcShape {
 // epilogue group when some tile needs it, and the staged addend buffers.
 static size_t tc_b_bytes(const TcShape& sh, bool res) {
   const int KS = (sh.r + 4) >> 2;
-  return (size_t)(res ? (KS + 1) / 2 : 2) * sh.MT * 16 * 64;
+  return (size_t)(res ? (KS + 1) / 2 : 4) * sh.MT * 16 * 64;
 }
 static size_t tc_smem_bytes(const TcShape& sh, int add_limbs, bool res) {
   return (size_t)kTcHead + sh.const_bytes + kTcFsx + (size_t)kTcNX * kTcXStage + 2 * (size_t)kTcAStage * (res ? 2 : 1) +
-         tc_b_bytes(sh, res) + (sh.limb ? 2 * (size_t)sh.MT * 4 * kTcRows * 4 : 0) + (size_t)sh.nadd * add_limbs * 512;
+         tc_b_bytes(sh, res) + (sh.limb ? 2 * (size_t)(4 * sh.MT - sh.lbase) * kTcRows * 4 : 0) +
+         (size_t)sh.nadd * add_limbs * 512;
 }
 
 // RES: B (all 4(r + 1) digits of every output column) stays in shared memory
@@ -516,8 +518,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t* X = smem + kTcHead + sh.const_bytes + kTcFsx;
   uint8_t* A = X + kTcNX * kTcXStage;
   uint8_t* B = A + 2 * kAStage;
-  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + (size_t)(RES ? (KS + 1) / 2 : 2) * bslice);
-  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (sh.limb ? (size_t)2 * 4 * MT * kTcRows : 0));
+  uint32_t* LIMB = reinterpret_cast<uint32_t*>(B + (size_t)(RES ? (KS + 1) / 2 : 4) * bslice);
+  const int lcol = 4 * MT - sh.lbase;  // limbs held per coefficient in a limb column
+  uint8_t* ADD = reinterpret_cast<uint8_t*>(LIMB + (sh.limb ? (size_t)2 * lcol * kTcRows : 0));
   const uint32_t bar0 = smem_addr(smem);
   auto x_full = [&](int s) { return bar0 + 8u * s; };
   auto x_empty = [&](int s) { return bar0 + 8u * (3 + s); };
@@ -621,15 +624,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           bulk_g2s(smem_addr(B + (size_t)c2 * bslice), bmat + (size_t)c2 * pmax * 32, bslice, b_full(0));
       }
     } else if (lane == 0) {
-      // B slices (K 32 each, two per chunk), the same sequence for every tile
+      // B: per chunk one stage of two K 32 slices (K 64), the same sequence for every tile
       int gb = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x)
-        for (int c2 = 0; c2 < 2 * nch; ++c2, ++gb) {
+        for (int c = 0; c < nch; ++c, ++gb) {
           const int sb = gb & 1;
           if (gb >= 2 && !(ok = mbar_wait(b_empty(sb), (uint32_t)((gb >> 1) - 1) & 1u))) break;
-          mbar_expect_tx(b_full(sb), bslice);
-          bulk_g2s(smem_addr(B + sb * bslice), bmat + (size_t)c2 * pmax * 32, bslice, b_full(sb));
+          mbar_expect_tx(b_full(sb), 2u * bslice);
+          for (int h = 0; h < 2; ++h)
+            bulk_g2s(smem_addr(B + (size_t)(2 * sb + h) * bslice), bmat + (size_t)(2 * c + h) * pmax * 32, bslice,
+                     b_full(sb));
         }
     }
   } else if (warp == kTcWarpMma) {
@@ -678,20 +683,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
             const uint64_t adesc = adesc0 + (uint64_t)((s * kAStage) >> 4);
             const int nks = min(4, KS - 4 * c);
-            for (int h = 0; h < 2; ++h) {
-              const int gb = 2 * g + h, sb = gb & 1;
-              if (!(ok = mbar_wait(b_full(sb), (uint32_t)(gb >> 1) & 1u))) break;
-              const uint64_t bdesc = bdesc0 + (uint64_t)((sb * bslice) >> 4);
-              const int ke = min(nks, 2 * h + 2);
-              for (int ks = 2 * h; ks < ke; ++ks) {
-                const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
-                const uint64_t da = adesc + (uint64_t)(16 * ks);            // + 256 B per k-step
-                const uint64_t db = bdesc + (uint64_t)(16 * (ks & 1));      // + 256 B per k-step
-                tc_mma(dbase, da, db, idesc0, accum);
-                if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
-              }
-              tc_commit(b_empty(sb));
+            const int sb = g & 1;  // B stage of this chunk (one per chunk, like A)
+            if (!(ok = mbar_wait(b_full(sb), (uint32_t)(g >> 1) & 1u))) break;
+            const uint64_t bdesc = bdesc0 + (uint64_t)((2u * (uint32_t)sb * bslice) >> 4);
+            for (int ks = 0; ks < nks; ++ks) {
+              const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+              const uint64_t da = adesc + (uint64_t)(16 * ks);  // + 256 B per k-step
+              const uint64_t db = bdesc + (uint64_t)((ks >> 1) * (bslice >> 4) + 16 * (ks & 1));
+              tc_mma(dbase, da, db, idesc0, accum);
+              if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
             }
+            tc_commit(b_empty(sb));
             tc_commit(a_empty(s));
           }
         }
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int e = tid - 32 * kTcYWarps;
     const int eg = e >> 7, ec = e & (kTcRows - 1);
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    uint32_t* limb = LIMB + (size_t)eg * 4 * MT * kTcRows + ec;
+    uint32_t* limb = LIMB + (size_t)eg * lcol * kTcRows + ec - (size_t)sh.lbase * kTcRows;  // index by limb l
     int tl = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
@@ -891,7 +893,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         rs.finish(4 * MT);
       } else {
-        crt_epilogue(LIMB + (size_t)eg * 4 * MT * kTcRows, ec, kTcRows, 4 * MT, epi, poly, b, n0 + ec, N, out,
+        crt_epilogue(LIMB + (size_t)eg * lcol * kTcRows, ec, kTcRows, 4 * MT, epi, poly, b, n0 + ec, N, out,
                      out_pstride, out_bstride, add_s, kTcRows);
       }
       if (sh.nadd) mbar_arrive(add_empty(eg));
@@ -969,6 +971,14 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
     const bool streamed = (epi.kind == Epi::kStore && !has_add && !smallp) ||
                           (epi.kind == Epi::kRelin && epi.shift > 0 && !smallp);
     if (!streamed) sh.limb = 1;
+  }
+  // when every tile is a relinearisation stream, a limb column starts at its rounding limb
+  sh.lbase = 0;
+  if (epi.kind == Epi::kRelin && epi.shift > 0) {
+    bool all_stream = true;
+    for (int p = 0; p < npoly; ++p)
+      if (p == 0 ? epi.small != nullptr : (p == 1 ? epi.small1 != nullptr : false)) all_stream = false;
+    if (all_stream) sh.lbase = min((epi.shift - 1) >> 5, epi.shift >> 5);
   }
   constexpr size_t kSmemMax = 227 * 1024;
   sh.nadd = 0;

@@ -527,7 +527,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto a_full = [&](int s) { return bar0 + 8u * (6 + s); };
   auto a_empty = [&](int s) { return bar0 + 8u * (8 + s); };
   auto b_full = [&](int s) { return bar0 + 8u * (10 + s); };
-  auto b_empty = [&](int s) { return bar0 + 8u * (12 + s); };
   // per tile parity (= epilogue group): each completes once every two tiles
   auto acc_full = [&](int s) { return bar0 + 8u * (14 + s); };
   auto acc_empty = [&](int s) { return bar0 + 8u * (16 + s); };
@@ -548,10 +547,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(x_empty(s), 32 * kTcYWarps);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(a_full(s), 32 * kTcYWarps);
+      // streamed B shares the A stage barriers: full after the digit warps and the
+      // B copies (one arrival with its bytes), empty after one MMA commit
+      mbar_init(a_full(s), 32 * kTcYWarps + (RES ? 0 : 1));
       mbar_init(a_empty(s), 1);
-      mbar_init(b_full(s), 1);
-      mbar_init(b_empty(s), 1);
+      mbar_init(b_full(s), 1);  // resident B: all of it, once
       mbar_init(acc_full(s), 1);
       mbar_init(acc_empty(s), kTcRows);
       mbar_init(add_full(s), 1);
@@ -630,11 +630,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x)
         for (int c = 0; c < nch; ++c, ++gb) {
           const int sb = gb & 1;
-          if (gb >= 2 && !(ok = mbar_wait(b_empty(sb), (uint32_t)((gb >> 1) - 1) & 1u))) break;
-          mbar_expect_tx(b_full(sb), 2u * bslice);
+          if (gb >= 2 && !(ok = mbar_wait(a_empty(sb), (uint32_t)((gb >> 1) - 1) & 1u))) break;
+          mbar_expect_tx(a_full(sb), 2u * bslice);
           for (int h = 0; h < 2; ++h)
             bulk_g2s(smem_addr(B + (size_t)(2 * sb + h) * bslice), bmat + (size_t)(2 * c + h) * pmax * 32, bslice,
-                     b_full(sb));
+                     a_full(sb));
         }
     }
   } else if (warp == kTcWarpMma) {
@@ -683,9 +683,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!(ok = mbar_wait(a_full(s), (uint32_t)(g >> 1) & 1u))) break;
             const uint64_t adesc = adesc0 + (uint64_t)((s * kAStage) >> 4);
             const int nks = min(4, KS - 4 * c);
-            const int sb = g & 1;  // B stage of this chunk (one per chunk, like A)
-            if (!(ok = mbar_wait(b_full(sb), (uint32_t)(g >> 1) & 1u))) break;
-            const uint64_t bdesc = bdesc0 + (uint64_t)((2u * (uint32_t)sb * bslice) >> 4);
+            const uint64_t bdesc = bdesc0 + (uint64_t)((2u * (uint32_t)s * bslice) >> 4);  // B stage = A stage
             for (int ks = 0; ks < nks; ++ks) {
               const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
               const uint64_t da = adesc + (uint64_t)(16 * ks);  // + 256 B per k-step
@@ -693,7 +691,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tc_mma(dbase, da, db, idesc0, accum);
               if (nsplit > 1) tc_mma(dbase + col1, da, db + boff1, idesc1, accum);
             }
-            tc_commit(b_empty(sb));
             tc_commit(a_empty(s));
           }
         }

@@ -430,7 +430,9 @@ __global__ void __launch_bounds__(16 * kRowsPerCta, 5) k_ntt_rows_tensor(uint32_
   __shared__ uint32_t s[kRowsPerCta * 4 * kSlot];
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
-  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  // ciphertext fastest within a prime: consecutive CTAs reuse the prime's twiddles (and key rows) from L2
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
   const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
   const size_t rowN = (size_t)r * N;
   const int c = blockIdx.x * kRowsPerCta + sub;
@@ -474,7 +476,9 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
   __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
-  const int b = blockIdx.y / r, p = blockIdx.y - b * r;
+  // ciphertext fastest within a prime: consecutive CTAs reuse the prime's twiddles (and key rows) from L2
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
   const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
   const int c = blockIdx.x * kRowsPerCta + sub;
   const size_t coff = (size_t)c * kRowLen;

@@ -378,7 +378,8 @@ constexpr int kTcNX = 3;                    // residue stages
 constexpr int kTcXStage = 16 * kTcRows * 4; // bytes: 16 primes x 128 coefficients
 constexpr int kTcAStage = kTcRows * 64 * 2; // bytes: 128 rows x K 64 f16
 constexpr int kTcHead = 1024;               // mbarriers + TMEM address
-constexpr int kTcFsx = 2048;                // quotient partial sums, [tile parity][half][row]
+constexpr int kTcFsx = 4096;                // quotient partial sums [tile parity][half][row] (floats),
+                                            // then epilogue carries [tile parity][row] (int64)
 
 // Balanced bytes of y < 2^31 (y < q) as two f16x2 registers {d0, d1}, {d2, d3}:
 // e = y + 0x808080, d_a = byte_a(e) - 128 for a < 3, d_3 = byte_3(e) <= 128.
@@ -462,6 +463,84 @@ struct RelinStream {
   }
 };
 
+// Configures the relinearisation stream of one coefficient (kRelin epilogue):
+// shift s = epi.shift (round at bit s - 1), result mod 2^ob plus the addend
+// (staged in shared memory with row stride kTcRows when add_s is given, else
+// read from global), then the rescale by epi.k2 bits.
+__device__ __forceinline__ void relin_setup(RelinStream& rs, const EpiArgs& epi, int ob, bool has_add,
+                                            const uint32_t* add_s, int b, int poly, int n, int N, uint32_t* dst) {
+  const int sft = epi.shift;
+  rs.sl = sft >> 5;
+  rs.sb = sft & 31;
+  rs.rl = (sft - 1) >> 5;
+  rs.rbit = (sft - 1) & 31;
+  const int nlo = (ob + 31) >> 5;
+  rs.nz = nlo;
+  rs.zmask = limb_mask(nlo - 1, ob);
+  rs.add = has_add ? (add_s ? add_s : epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n)
+                   : nullptr;
+  rs.add_limbs = epi.add_limbs;
+  rs.add_stride = add_s ? kTcRows : N;
+  rs.k2 = epi.k2;
+  rs.kl = epi.k2 >> 5;
+  rs.kb = epi.k2 & 31;
+  rs.rl2 = epi.k2 > 0 ? (epi.k2 - 1) >> 5 : 0;
+  rs.rbit2 = epi.k2 > 0 ? (epi.k2 - 1) & 31 : 0;
+  const int fb = ob - epi.k2;
+  rs.nf = (fb + 31) >> 5;
+  rs.wmask = limb_mask(rs.nf - 1, fb);
+  rs.out_limbs = epi.out_limbs;
+  rs.dst = dst;
+  rs.N = N;
+}
+
+// The relinearisation epilogue over a limb column held in shared memory
+// (col[l kTcRows] for l in [min(rl, sl), nx), the exact product X after its
+// carries): the same result as RelinStream, in passes whose loads do not wait
+// on a carry.  In place: the z limbs overwrite the x limbs they replace.
+//   z_j = ((X + 2^(s-1)) >> s) limb j + addend limb j, mod 2^ob;
+//   out = (Z + 2^(k2-1)) >> k2 mod 2^(ob-k2) (or Z when k2 = 0), zero-padded.
+__device__ __forceinline__ void relin_column(uint32_t* col, int nx, const EpiArgs& epi, int ob, const uint32_t* add,
+                                             int add_stride, uint32_t* dst, int N) {
+  const int s = epi.shift, sl = s >> 5, sb = s & 31, rl = (s - 1) >> 5, rbit = (s - 1) & 31;
+  const int nz = (ob + 31) >> 5;
+  const uint32_t zmask = limb_mask(nz - 1, ob);
+  const int na = add ? epi.add_limbs : 0;
+  uint32_t cA = (col[(size_t)rl * kTcRows] >> rbit) & 1u, cB = 0u;
+#pragma unroll 4
+  for (int j = 0; j < nz; ++j) {
+    const uint32_t x0 = sl + j < nx ? col[(size_t)(sl + j) * kTcRows] : 0u;
+    const uint32_t x1 = sl + j + 1 < nx ? col[(size_t)(sl + j + 1) * kTcRows] : 0u;
+    const uint32_t a = j < na ? add[(size_t)j * add_stride] : 0u;
+    const uint32_t y = __funnelshift_r(x0, x1, sb) + cA;
+    cA = y < cA ? 1u : 0u;
+    const uint64_t zz = (uint64_t)y + a + cB;
+    cB = (uint32_t)(zz >> 32);
+    uint32_t z = (uint32_t)zz;
+    if (j == nz - 1) z &= zmask;
+    col[(size_t)(sl + j) * kTcRows] = z;
+  }
+  const int out_limbs = epi.out_limbs;
+  if (epi.k2 == 0) {
+    for (int i = 0; i < out_limbs; ++i) dst[(size_t)i * N] = i < nz ? col[(size_t)(sl + i) * kTcRows] : 0u;
+    return;
+  }
+  const int k2 = epi.k2, kl = k2 >> 5, kb = k2 & 31, rl2 = (k2 - 1) >> 5, rbit2 = (k2 - 1) & 31;
+  const int fb = ob - k2, nf = (fb + 31) >> 5;
+  const uint32_t wmask = limb_mask(nf - 1, fb);
+  uint32_t cC = rl2 < nz ? (col[(size_t)(sl + rl2) * kTcRows] >> rbit2) & 1u : 0u;
+#pragma unroll 4
+  for (int i = 0; i < nf; ++i) {
+    const uint32_t z0 = kl + i < nz ? col[(size_t)(sl + kl + i) * kTcRows] : 0u;
+    const uint32_t z1 = kl + i + 1 < nz ? col[(size_t)(sl + kl + i + 1) * kTcRows] : 0u;
+    uint32_t w = __funnelshift_r(z0, z1, kb) + cC;
+    cC = w < cC ? 1u : 0u;
+    if (i == nf - 1) w &= wmask;
+    if (i < out_limbs) dst[(size_t)i * N] = w;
+  }
+  for (int i = nf; i < out_limbs; ++i) dst[(size_t)i * N] = 0u;
+}
+
 struct TcShape {
   int r, MT, nblk, npoly, ntiles;  // primes, output m-tiles, 128-blocks per polynomial, tiles
   int acc_cols, nacc;              // TMEM columns per accumulator, accumulators
@@ -470,6 +549,7 @@ struct TcShape {
   int limb;                        // 1: a limb column per epilogue group (some tile drains TMEM first)
   int exact22;                     // 1: every column sum is below 2^22 (fp32 -> int by one exact addition)
   int lbase;                       // first limb a limb column holds (limbs below only feed the carry)
+  int split;                       // 1: both epilogue groups drain every tile (relinearisation, one accumulator)
 };
 
 // Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
@@ -533,6 +613,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto add_full = [&](int s) { return bar0 + 8u * (18 + s); };
   auto add_empty = [&](int s) { return bar0 + 8u * (20 + s); };
   auto fsx_bar = [&](int s) { return bar0 + 8u * (22 + s); };  // per tile parity: Y partial sums written
+  auto limb_full = [&](int s) { return bar0 + 8u * (24 + s); };   // split: both halves of a limb column written
+  auto limb_empty = [&](int s) { return bar0 + 8u * (26 + s); };  // split: the column has been streamed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 512);
   auto tile_of = [&](int t, int& n0, int& poly, int& b) {
     const int py = t / sh.nblk;
@@ -553,7 +635,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(a_empty(s), 1);
       mbar_init(b_full(s), 1);  // resident B: all of it, once
       mbar_init(acc_full(s), 1);
-      mbar_init(acc_empty(s), kTcRows);
+      mbar_init(acc_empty(s), sh.split ? 2 * kTcRows : kTcRows);
+      mbar_init(limb_full(s), 2 * kTcRows);
+      mbar_init(limb_empty(s), kTcRows);
       mbar_init(add_full(s), 1);
       mbar_init(add_empty(s), kTcRows);
       mbar_init(fsx_bar(s), 32 * kTcYWarps);
@@ -771,7 +855,90 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t* limb = LIMB + (size_t)eg * lcol * kTcRows + ec - (size_t)sh.lbase * kTcRows;  // index by limb l
     int tl = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
+    // column sums (exact integers in fp32) -> 32-bit limbs, 16 columns (4 limbs) per TMEM load:
+    // limb l = sum_u S_{4l+u} 256^u + carry.  With |S| < 2^22 the low mantissa bits of
+    // S + 1.5 2^23 are S (one FADD), else cvt.rni.
+    auto limbs16 = [&](auto exact, uint32_t taddr, long long& carry, auto&& emit, int m) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      int sv[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        sv[u] = decltype(exact)::value ? __float_as_int(__uint_as_float(v[u]) + 12582912.0f) - 0x4B400000
+                                       : __float2int_rn(__uint_as_float(v[u]));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long val = carry + (long long)sv[4 * q] + (long long)sv[4 * q + 1] * 256LL +
+                              (long long)sv[4 * q + 2] * 65536LL + (long long)sv[4 * q + 3] * 16777216LL;
+        carry = val >> 32;
+        emit(4 * m + q, (uint32_t)val);
+      }
+    };
+    if (sh.split) {
+      // Relinearisation with one accumulator: both groups drain every tile, group 0 the low
+      // column half (its carry out goes through shared memory), group 1 the high half with a
+      // zero carry in.  Group (tile & 1) then streams the tile's limb column, adding that carry
+      // at limb lsplit, while the MMAs fill the accumulator again: the MMAs wait for half a
+      // drain instead of a whole one.
+      const int mh = min(MT, max((MT + 1) >> 1, (sh.lbase + 3) >> 2));  // limbs >= 4 mh >= lbase are stored
+      const int lsplit = 4 * mh;
+      const int m0 = eg ? mh : 0, m1 = eg ? MT : mh;
+      long long* CAR = reinterpret_cast<long long*>(FSX + 4 * kTcRows);  // [tile parity][row]
+      for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
+        const int par = tl & 1;
+        ok = ok && mbar_wait(acc_full(par), (uint32_t)(tl >> 1) & 1u);
+        if (tl >= 2) ok = ok && mbar_wait(limb_empty(par), (uint32_t)((tl >> 1) - 1) & 1u);
+        ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t base = tmem + lane_off;  // the single accumulator
+        uint32_t* col = LIMB + (size_t)par * lcol * kTcRows + ec - (size_t)sh.lbase * kTcRows;
+        long long carry = 0;
+        auto emit = [&](int l, uint32_t x) {
+          if (l >= sh.lbase) col[(size_t)l * kTcRows] = x;
+        };
+        for (int m = m0; m < m1; ++m) {
+          if (sh.exact22)
+            limbs16(std::true_type{}, base + 16u * (uint32_t)m, carry, emit, m);
+          else
+            limbs16(std::false_type{}, base + 16u * (uint32_t)m, carry, emit, m);
+        }
+        if (eg == 0) CAR[par * kTcRows + ec] = carry;
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(acc_empty(par));
+        mbar_arrive(limb_full(par));
+        if (par != eg) continue;
+        int n0, poly, b;
+        tile_of(t, n0, poly, b);
+        if (!(ok = mbar_wait(limb_full(par), (uint32_t)(tl >> 1) & 1u))) break;
+        if (sh.nadd && !(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
+        const int ob = epi.item_bits ? __ldg(epi.item_bits + b) : epi.out_bits;
+        const bool has_add = epi.add && poly < epi.add_polys;
+        const uint32_t* add_s =
+            sh.nadd ? reinterpret_cast<const uint32_t*>(ADD + (size_t)(tl % sh.nadd) * add_limbs * 512) + ec : nullptr;
+        uint32_t* dst = out + (size_t)b * out_bstride + (size_t)poly * out_pstride + n0 + ec;
+        // group 0's carry into the high half
+        long long c = CAR[par * kTcRows + ec];
+        for (int l = lsplit; l < 4 * MT; ++l) {
+          const long long v = (long long)col[(size_t)l * kTcRows] + c;
+          col[(size_t)l * kTcRows] = (uint32_t)v;
+          c = v >> 32;
+        }
+        const uint32_t* add = has_add ? (add_s ? add_s
+                                               : epi.add + (size_t)b * epi.add_bstride +
+                                                     (size_t)poly * epi.add_pstride + n0 + ec)
+                                      : nullptr;
+        relin_column(col, 4 * MT, epi, ob, add, add_s ? kTcRows : N, dst, N);
+        if (sh.nadd) mbar_arrive(add_empty(eg));
+        mbar_arrive(limb_empty(par));
+      }
+    }
+    for (int t = blockIdx.x; t < sh.ntiles && !sh.split; t += gridDim.x, ++tl) {
       if ((tl & 1) != eg) continue;
       int n0, poly, b;
       tile_of(t, n0, poly, b);
@@ -795,31 +962,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t* dst = out + (size_t)b * out_bstride + (size_t)poly * out_pstride + n0 + ec;
       const int nlo = (ob + 31) >> 5;
       RelinStream rs;
-      if (mode == 2) {
-        const int sft = epi.shift;
-        rs.sl = sft >> 5;
-        rs.sb = sft & 31;
-        rs.rl = (sft - 1) >> 5;
-        rs.rbit = (sft - 1) & 31;
-        rs.nz = nlo;
-        rs.zmask = limb_mask(nlo - 1, ob);
-        rs.add = has_add ? (add_s ? add_s
-                                  : epi.add + (size_t)b * epi.add_bstride + (size_t)poly * epi.add_pstride + n0 + ec)
-                         : nullptr;
-        rs.add_limbs = epi.add_limbs;
-        rs.add_stride = add_s ? kTcRows : N;
-        rs.k2 = epi.k2;
-        rs.kl = epi.k2 >> 5;
-        rs.kb = epi.k2 & 31;
-        rs.rl2 = epi.k2 > 0 ? (epi.k2 - 1) >> 5 : 0;
-        rs.rbit2 = epi.k2 > 0 ? (epi.k2 - 1) & 31 : 0;
-        const int fb = ob - epi.k2;
-        rs.nf = (fb + 31) >> 5;
-        rs.wmask = limb_mask(rs.nf - 1, fb);
-        rs.out_limbs = epi.out_limbs;
-        rs.dst = dst;
-        rs.N = N;
-      }
+      if (mode == 2) relin_setup(rs, epi, ob, has_add, add_s, b, poly, n0 + ec, N, dst);
       bool have_add_stage = false;
       if (direct && mode == 2 && sh.nadd) {
         if (!(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;
@@ -977,6 +1120,8 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
       if (p == 0 ? epi.small != nullptr : (p == 1 ? epi.small1 != nullptr : false)) all_stream = false;
     if (all_stream) sh.lbase = min((epi.shift - 1) >> 5, epi.shift >> 5);
   }
+  // one accumulator and every tile a relinearisation stream: both epilogue groups drain each tile
+  sh.split = (sh.nacc == 1 && sh.lbase > 0) ? 1 : 0;
   constexpr size_t kSmemMax = 227 * 1024;
   sh.nadd = 0;
   const bool res = tc_smem_bytes(sh, add_limbs, true) <= kSmemMax;

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
 // accesses conflict-free, and the twiddle of a butterfly depends only on the
 // row, so twiddle loads are warp-wide broadcasts.
 template <int LOGN1>
-__global__ void __launch_bounds__(2 << LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
                                                              const uint2* __restrict__ tw,
                                                              const uint32_t* __restrict__ qtab) {
   constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;

@@ -551,17 +551,6 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
   return FHE_OK;
 }
 
-static void cols_fwd_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, cudaStream_t st) {
-  const int logN = ctx->prm.logN, logN1 = logN - 8;
-  dim3 gcols(kRowLen / 32, rows);
-#define FHE_NTT_COLS_F(L)                                                                          \
-  case L:                                                                                          \
-    k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi2, ctx->d_q); \
-    break;
-  switch (logN1) { FHE_NTT_COLS_F(5) FHE_NTT_COLS_F(6) FHE_NTT_COLS_F(7) FHE_NTT_COLS_F(8) }
-#undef FHE_NTT_COLS_F
-}
-
 static void cols_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
                         cudaStream_t st) {
   const int logN = ctx->prm.logN, logN1 = logN - 8;

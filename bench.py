@@ -93,6 +93,22 @@ def oracle_throughput(steps: int, warmup: int, workers: int):
     return steps / wall, wall, per
 
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The job's time for a timed region: the slowest rank's (`dist` None: one process)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, steps: int, ms: float) -> float:
+    """Whole-job units/s: every rank processes its own batch of units each step (weak scaling)."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -350,12 +366,10 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = fhe.fhe_profile_read(ctx)
     fhe.fhe_profile_reset(ctx, False)
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * cnum * args.steps / (ms / 1e3)
+    value = job_throughput(world, cnum, args.steps, ms)
     launches = sum(n for n, _ in prof.values())
 
     # end to end: pinned host inputs -> device, compute, result -> host, every step.  The batch
@@ -415,11 +429,8 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * cnum * args.e2e_steps / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(ms_e2e, dist, "cuda")
+    e2e_value = job_throughput(world, cnum, args.e2e_steps, ms_e2e)
     h2d = A_h.numel() * 4 + B_h.numel() * 4
     d2h = out_h.numel() * 4
 

@@ -199,6 +199,24 @@ def test_full_size_north_star_pair():
 
 
 @pytest.mark.slow
+def test_bench_configuration_sampled_pairs_match_the_oracle():
+    """The benchmark's launch configuration (N = 2^16, logQ = logP = 1200, 64 pairs in one call):
+    two pairs sampled from the batch, every limb compared with the oracle."""
+    P = make_pair(16, 1200, 1200, seed=64)
+    N = P.prm.N
+    la = random_ct_limbs(P.g, 64, N, 1200)
+    lb = random_ct_limbs(P.g, 64, N, 1200)
+    out = P.ctx.mult_relin_rescale(_ct_from_limbs(P, la, 1200), _ct_from_limbs(P, lb, 1200), 40)
+    host = out.data.cpu().numpy().view(np.uint32)
+    P.ctx.close()
+    for c in (0, 45):  # a pair from the first tiles and one from the persistent CTAs' later sweeps
+        got = tuple(bigint.from_limbs(host[c, p]) for p in range(2))
+        want = tuple(ckks.rescale(ckks.mult(_oracle_ct(la[c:c + 1])[0], _oracle_ct(lb[c:c + 1])[0], P.evk, 1200, 1200),
+                                  40, 1200))
+        assert got == want, c
+
+
+@pytest.mark.slow
 def test_full_size_batch_tensor_core_crt_equals_integer_crt():
     """N = 2^16, logQ = logP = 1200, cnum 8: the tensor-core and integer reconstructions agree on every limb."""
     import paper_2607_05920_gb300 as fhe

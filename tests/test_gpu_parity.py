@@ -178,7 +178,7 @@ def test_two_pass_ring_mid_size(crt):
 
 
 @pytest.mark.slow
-def test_full_size_north_star_pair():
+def test_full_size_pair_every_limb():
     """N = 2^16, logQ = logP = 1200, scale 2^40: one pair, every limb compared with the oracle."""
     import paper_2607_05920_gb300 as fhe
 

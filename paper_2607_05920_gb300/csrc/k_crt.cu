@@ -541,6 +541,24 @@ __device__ __forceinline__ void relin_column(uint32_t* col, int nx, const EpiArg
   for (int i = nf; i < out_limbs; ++i) dst[(size_t)i * N] = 0u;
 }
 
+// Limb partial S0 + 2^8 S1 + 2^16 S2 + 2^24 S3 of four exact column sums
+// |S_u| < 2^22 held as fp32 in v: the bits of S + 1.5 2^23 are 0x4B400000 + S,
+// so two 32-bit wrap-around sums (each exact as int32) and one 64-bit
+// combine give it; K = -257 * 0x4B400000 mod 2^32 removes the offsets.
+__device__ __forceinline__ long long limb_partial_exact(const uint32_t* v) {
+  uint32_t a[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) a[u] = __float_as_uint(__uint_as_float(v[u]) + 12582912.0f);
+  const uint32_t lo = a[0] + (a[1] << 8) + 0x74C00000u;
+  const uint32_t hi = a[2] + (a[3] << 8) + 0x74C00000u;
+  return (long long)(int32_t)lo + ((long long)(int32_t)hi << 16);
+}
+__device__ __forceinline__ long long limb_partial_cvt(const uint32_t* v) {
+  return (long long)__float2int_rn(__uint_as_float(v[0])) + (long long)__float2int_rn(__uint_as_float(v[1])) * 256LL +
+         (long long)__float2int_rn(__uint_as_float(v[2])) * 65536LL +
+         (long long)__float2int_rn(__uint_as_float(v[3])) * 16777216LL;
+}
+
 struct TcShape {
   int r, MT, nblk, npoly, ntiles;  // primes, output m-tiles, 128-blocks per polynomial, tiles
   int acc_cols, nacc;              // TMEM columns per accumulator, accumulators
@@ -866,15 +884,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      int sv[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u)
-        sv[u] = decltype(exact)::value ? __float_as_int(__uint_as_float(v[u]) + 12582912.0f) - 0x4B400000
-                                       : __float2int_rn(__uint_as_float(v[u]));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const long long val = carry + (long long)sv[4 * q] + (long long)sv[4 * q + 1] * 256LL +
-                              (long long)sv[4 * q + 2] * 65536LL + (long long)sv[4 * q + 3] * 16777216LL;
+        const long long val =
+            carry + (decltype(exact)::value ? limb_partial_exact(v + 4 * q) : limb_partial_cvt(v + 4 * q));
         carry = val >> 32;
         emit(4 * m + q, (uint32_t)val);
       }
@@ -982,15 +995,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
               : "r"(base + 16u * (uint32_t)m));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-          int sv[16];
-#pragma unroll
-          for (int u = 0; u < 16; ++u)
-            sv[u] = decltype(exact)::value ? __float_as_int(__uint_as_float(v[u]) + 12582912.0f) - 0x4B400000
-                                           : __float2int_rn(__uint_as_float(v[u]));
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const long long val = carry + (long long)sv[4 * q] + (long long)sv[4 * q + 1] * 256LL +
-                                  (long long)sv[4 * q + 2] * 65536LL + (long long)sv[4 * q + 3] * 16777216LL;
+            const long long val =
+                carry + (decltype(exact)::value ? limb_partial_exact(v + 4 * q) : limb_partial_cvt(v + 4 * q));
             carry = val >> 32;
             const int l = 4 * m + q;
             const uint32_t x = (uint32_t)val;

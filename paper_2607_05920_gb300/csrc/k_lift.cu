@@ -350,11 +350,12 @@ __global__ void __launch_bounds__(kLtThreads, 1)
         for (int j = 0; j < 4; ++j) {
           const int i = i0 + 4 * q4 + j;
           if (i < i1) {
-            // exact integers |S| < 2^22: the low mantissa bits of S + 1.5 2^23
-            int sv[4];
+            // exact integers |S| < 2^22: the bits of S + 1.5 2^23 are 0x4B400000 + S, so
+            // lo = S0 + 256 S1 = a0 + 256 a1 - 257 * 0x4B400000 (mod 2^32, exact as int32)
+            uint32_t sa[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) sv[a] = __float_as_int(__uint_as_float(v[4 * j + a]) + 12582912.0f) - 0x4B400000;
-            const int lo = sv[0] + sv[1] * 256, hi = sv[2] + sv[3] * 256;  // |.| < 2^31
+            for (int a = 0; a < 4; ++a) sa[a] = __float_as_uint(__uint_as_float(v[4 * j + a]) + 12582912.0f);
+            const int lo = (int)(sa[0] + (sa[1] << 8) + 0x74C00000u), hi = (int)(sa[2] + (sa[3] << 8) + 0x74C00000u);
             const uint4 k = PC[i];
             const uint64_t u = (uint64_t)((long long)lo + ((long long)hi << 16)) +
                                (((uint64_t)k.w << 32) | k.z);  // >= 0, < 2^49

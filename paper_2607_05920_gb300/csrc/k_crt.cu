@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       long long carry = 0;
       // column sums (exact integers in fp32) -> 32-bit limbs: limb l = sum_u S_{4l+u} 256^u + carry.
       // With |S| < 2^22 the low mantissa bits of S + 1.5 2^23 are S (one FADD), else cvt.rni.
-      auto drain = [&](auto exact) {
+      auto drain = [&](auto exact, auto&& emit) {
         for (int m = 0; m < MT; ++m) {
           uint32_t v[16];
           asm volatile(
@@ -1000,22 +1000,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const long long val =
                 carry + (decltype(exact)::value ? limb_partial_exact(v + 4 * q) : limb_partial_cvt(v + 4 * q));
             carry = val >> 32;
-            const int l = 4 * m + q;
-            const uint32_t x = (uint32_t)val;
-            if (!direct) {
-              if (l >= lfirst) limb[(size_t)l * kTcRows] = x;
-            } else if (mode == 1) {
-              if (l < epi.out_limbs) dst[(size_t)l * N] = l < nlo ? (x & limb_mask(l, ob)) : 0u;
-            } else {
-              rs.push_x(l, x);
-            }
+            emit(4 * m + q, (uint32_t)val);
           }
         }
       };
-      if (sh.exact22)
-        drain(std::true_type{});
-      else
-        drain(std::false_type{});
+      // the limb consumer is chosen once per tile
+      auto run = [&](auto&& emit) {
+        if (sh.exact22)
+          drain(std::true_type{}, emit);
+        else
+          drain(std::false_type{}, emit);
+      };
+      if (!direct) {
+        run([&](int l, uint32_t x) {
+          if (l >= lfirst) limb[(size_t)l * kTcRows] = x;
+        });
+      } else if (mode == 1) {
+        // X mod 2^ob: full limbs below the top one, the top one masked, zeros above
+        const uint32_t topmask = limb_mask(nlo - 1, ob);
+        const int olim = epi.out_limbs;
+        run([&](int l, uint32_t x) {
+          if (l < olim) dst[(size_t)l * N] = l < nlo - 1 ? x : (l == nlo - 1 ? (x & topmask) : 0u);
+        });
+      } else {
+        run([&](int l, uint32_t x) { rs.push_x(l, x); });
+      }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       mbar_arrive(acc_empty(eg));
       if (sh.nadd && !have_add_stage && !(ok = mbar_wait(add_full(eg), (uint32_t)(tl >> 1) & 1u))) break;

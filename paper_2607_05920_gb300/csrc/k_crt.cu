@@ -357,18 +357,24 @@ __global__ void __launch_bounds__(kCrtThreads, 3) k_crt_direct(const uint32_t* _
 // A tile = 128 coefficients of one polynomial = the MMA's M = the 128 TMEM
 // lanes.  The kernel is persistent (one CTA per SM walks the tiles) and warp
 // specialised, every hand-off an mbarrier:
-//   warps 0-3  (Y) y_i = [x_i (M/q_i)^-1]_{q_i} and kappa from the staged
-//              residues, as f16 digits into an A stage;
-//   warps 4-7  (E) per tile: S_p from the thread's own TMEM lane, carried into
-//              32-bit limbs, the accumulator released, then the epilogue;
-//   warps 16, 18  bulk copies (TMA engine): residue rows and the addend; B slices;
-//   warp 17    TMEM allocation and the MMA issue (one thread).
+//   warps 0-7   (Y) y_i = [x_i (M/q_i)^-1]_{q_i} and kappa from the staged
+//               residues (two threads per row), as f16 digits into an A stage;
+//   warps 8-15  (E) two groups of four: S_p from each thread's own TMEM lane,
+//               carried into 32-bit limbs, then the epilogue; the groups take
+//               alternate tiles, or (one accumulator, relinearisation) both
+//               drain every tile, a column half each;
+//   warp 16     residues by TMA tensor loads (16 primes x 128 coefficients)
+//               and an L2 prefetch of the next tile's;
+//   warp 17     TMEM allocation and the MMA issue (one thread);
+//   warp 18     B: streamed in K 64 stages, or loaded once when resident;
+//   warp 19     the staged addend of each tile (TMA tensor load).
 // With P <= 256 two accumulators alternate, so the epilogue of one tile runs
-// under the GEMM of the next.  K runs in chunks of 64 (16 primes).  Every
-// wait is bounded and reports a timeout through fhe_sync.
+// under the GEMM of the next.  K runs in chunks of 64 (16 primes), or 128
+// with B resident.  Every wait is bounded and reports a timeout through
+// fhe_sync.
 constexpr int kTcRows = 128;
 constexpr int kTcYWarps = 8;                // two threads per coefficient row
-constexpr int kTcEWarps = 8;                // two groups of four, alternating tiles
+constexpr int kTcEWarps = 8;                // two groups of four
 constexpr int kTcWarpProd = kTcYWarps + kTcEWarps;  // residues
 constexpr int kTcWarpMma = kTcWarpProd + 1;         // TMEM owner, MMA issue
 constexpr int kTcWarpProdB = kTcWarpMma + 1;        // B slices
@@ -570,10 +576,11 @@ struct TcShape {
   int split;                       // 1: both epilogue groups drain every tile (relinearisation, one accumulator)
 };
 
-// Shared memory of k_crt_tc: header, prime constants, quotient partial sums,
-// residue stages, two A stages (K 64, or K 128 with B resident), B (two K 32
-// slices streamed per chunk, or all of it resident), one limb column per
-// epilogue group when some tile needs it, and the staged addend buffers.
+// Shared memory of k_crt_tc: header, prime constants, quotient partial sums
+// and epilogue carries, residue stages, two A stages (K 64, or K 128 with B
+// resident), B (two stages of two K 32 slices, one stage per chunk, or all of
+// it resident), one limb column per epilogue group (per tile parity when both
+// groups drain every tile) when some tile needs it, and the staged addends.
 static size_t tc_b_bytes(const TcShape& sh, bool res) {
   const int KS = (sh.r + 4) >> 2;
   return (size_t)(res ? (KS + 1) / 2 : 4) * sh.MT * 16 * 64;

@@ -4,10 +4,12 @@
 // by limb-wise accumulation with the precomputed constants 2^(32 l) mod q_i
 // (Sec. 5 "Precomputed RNS Conversion Constants") and one final reduction.
 //
-// One thread owns one coefficient: its limbs sit in registers (read once,
-// coalesced across the warp), and it loops over all primes, writing one
-// coalesced residue row per prime.  The constant table of the CTA's primes is
-// staged in shared memory and read as warp-wide broadcasts.
+// Integer form (the Garner and integer-pipe reconstruction modes): one thread
+// owns one coefficient: its limbs sit in registers (read once, coalesced
+// across the warp), and it loops over all primes, writing one coalesced
+// residue row per prime.  The constant table of the CTA's primes is staged in
+// shared memory and read as warp-wide broadcasts.  The default form,
+// k_lift_tc below, runs the same sum as a byte-digit GEMM on the tensor cores.
 #include "common.cuh"
 
 namespace fhe {

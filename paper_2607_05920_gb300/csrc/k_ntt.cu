@@ -16,6 +16,12 @@
 // held in shared memory.  The global twiddle step of the paper is absorbed:
 // in the merged-twist CT network each stage already reads its own twiddle.
 // Rings with N <= 4096 run in one CTA (all stages in shared memory).
+//
+// Above that, a ring product (Sec. 5 pipeline: forward NTTs, pointwise
+// products, inverse NTTs) is three launches: the forward column stages, one
+// fused pass that finishes the forward transforms in each 256-word row, forms
+// the products there and runs the inverse row stages (the transform-domain
+// values never reach global memory), and the inverse column stages.
 #include "common.cuh"
 
 namespace fhe {

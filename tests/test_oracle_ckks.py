@@ -176,3 +176,84 @@ def test_encode_constant_closed_form():
     assert np.abs(encode.decode(m, N, 40, N // 2) - z).max() < 2.0 ** -30
     rot = ring.automorphism(m, 5)
     assert np.abs(encode.decode(rot, N, 40, N // 2) - np.roll(z, -1)).max() < 2.0 ** -30
+
+
+def test_moddown_by_hand_and_keeps_the_message():
+    # moddownBy reduces every coefficient mod 2^logQ' (no division, the scale is unchanged)
+    ct = ([5, (1 << 70) + 3, (1 << 80) - 1], [1 << 64, 7, (1 << 63) + 9])
+    assert ckks.moddown(ct, 64) == ([5, 3, (1 << 64) - 1], [0, 7, (1 << 63) + 9])
+    assert ckks.moddown(ct, 80) == (list(ct[0]), list(ct[1]))
+    # Dec_{Q'}(ct mod Q') = Dec_Q(ct) while the message and noise stay below Q'/2
+    g, prm, s, pk, _ = _setup(8, 120, 120, 9)
+    m = [int(x) for x in fs.small_signed(g, (), prm.N, 30)]
+    ct = _enc(g, prm, pk, m)
+    bound = 2 * prm.N * fs.TAIL + fs.TAIL
+    for lq in (97, 64, 33):
+        dec = ckks.decrypt(s, ckks.moddown(ct, lq), lq)
+        assert dec == ckks.decrypt(s, ct, prm.logQ)
+        assert max(abs(x - y) for x, y in zip(dec, m)) <= bound
+
+
+def _rotation_setup(seed, steps, logN=9, logQ=120, logP=120):
+    g, prm, s, pk, evk = _setup(logN, logQ, logP, seed)
+    rtk = {}
+    for step in steps:
+        a = bigint.from_limbs(fs.uniform_limbs(g, (), prm.N, prm.logQ + prm.logP))
+        e = [int(x) for x in fs.gaussian(g, (), prm.N)]
+        rtk[step] = ckks.rotation_key(prm, s, step, a, e)
+    return g, prm, s, pk, evk, rtk
+
+
+def test_negative_step_rotates_right():
+    g, prm, s, pk, _, rtk = _rotation_setup(21, (-1, -5, 5, 1))
+    n = prm.N // 2
+    # 5 * 5^-1 = 1 mod 2N, and 5^-j 5^j = 1
+    assert ckks.galois_element(prm.N, -1) * 5 % (2 * prm.N) == 1
+    assert ckks.galois_element(prm.N, -5) * ckks.galois_element(prm.N, 5) % (2 * prm.N) == 1
+    z = fs.unit_disk(g, n)
+    ct = _enc(g, prm, pk, encode.encode(z, prm.N, 40))
+    for step in (-1, -5):
+        out = ckks.rotate(ct, step, rtk[step], prm.N, prm.logQ, prm.logP)
+        dec = encode.decode(ckks.decrypt(s, out, prm.logQ), prm.N, 40, n)
+        assert np.abs(dec - np.roll(z, -step)).max() < 2.0 ** -20  # right rotation: np.roll(z, +|step|)
+    # rotating by -5 and then by +5 gives the slots back
+    back = ckks.rotate(ckks.rotate(ct, -5, rtk[-5], prm.N, prm.logQ, prm.logP), 5, rtk[5], prm.N, prm.logQ, prm.logP)
+    dec = encode.decode(ckks.decrypt(s, back, prm.logQ), prm.N, 40, n)
+    assert np.abs(dec - z).max() < 2.0 ** -20
+
+
+@pytest.mark.parametrize("logQl", [97, 64, 33])
+def test_key_switching_below_the_top_level(logQl):
+    """Relinearisation at a lower level Q_l with the top-level key (reduced mod P Q_l): the two-component
+    decryption equals the three-component one up to the key-switch error, also at ragged levels."""
+    g, prm, s, pk, evk = _setup(8, 120, 120, 30 + logQl)
+    m1 = [int(x) for x in fs.small_signed(g, (), prm.N, 12)]
+    m2 = [int(x) for x in fs.small_signed(g, (), prm.N, 12)]
+    c1 = ckks.moddown(_enc(g, prm, pk, m1), logQl)
+    c2 = ckks.moddown(_enc(g, prm, pk, m2), logQl)
+    d0, d1, d2 = ckks.tensor(c1, c2, logQl)
+    ct = ckks.relinearize(d0, d1, d2, evk, logQl, prm.logP)
+    Q = 1 << logQl
+    s2 = ring.negacyclic_mul(s, s)
+    three = ring.mod_poly(ring.add_poly(ring.add_poly(d0, ring.negacyclic_mul(d1, s)), ring.negacyclic_mul(d2, s2)), Q)
+    two = ring.mod_poly(ring.add_poly(ct[0], ring.negacyclic_mul(ct[1], s)), Q)
+    diff = [(x - y) % Q for x, y in zip(two, three)]
+    diff = [d - Q if 2 * d > Q else d for d in diff]
+    # |d2 e'| / P + rounding <= N Q_l 19 / P + (1 + N) / 2 (P = 2^120 > Q_l)
+    bound = prm.N * fs.TAIL * Q // prm.P + 1 + prm.N
+    assert max(abs(d) for d in diff) <= bound
+    # and a key for the wrong secret would not pass: the error would be of size Q_l
+    if logQl >= 64:
+        dec = ckks.decrypt(s, ct, logQl)
+        want = ring.negacyclic_mul(m1, m2)
+        assert max(abs(x - y) for x, y in zip(dec, want)) < 1 << 40
+
+
+def test_rotation_below_the_top_level():
+    g, prm, s, pk, _, rtk = _rotation_setup(22, (3,))
+    n = prm.N // 2
+    z = fs.unit_disk(g, n)
+    ct = ckks.moddown(_enc(g, prm, pk, encode.encode(z, prm.N, 40)), 97)
+    out = ckks.rotate(ct, 3, rtk[3], prm.N, 97, prm.logP)
+    dec = encode.decode(ckks.decrypt(s, out, 97), prm.N, 40, n)
+    assert np.abs(dec - np.roll(z, -3)).max() < 2.0 ** -20

@@ -206,3 +206,43 @@ def test_centered_tie_and_range():
     assert crt.centered(8, 16) == 8  # x = Q/2 stays positive (strict '>')
     assert crt.centered(9, 16) == -7
     assert crt.centered(7, 15) == 7 and crt.centered(8, 15) == -7
+
+
+# ---- the exact product at the operand widths of the key switch at N = 2^16, logQ = logP = 1200 (and 1550):
+# d2 (logQ bits) times a key polynomial (logP + logQ bits) needs about 3,616 bits and ~60 62-bit primes in
+# fastmul.c; these regimes are checked against schoolbook, Kronecker and a closed form.
+
+@pytest.mark.parametrize("bits_a,bits_b", [(1200, 1200), (2400, 2400), (1200, 2400), (1550, 3100)])
+def test_fast_matches_schoolbook_at_key_switch_widths(bits_a, bits_b):
+    g = fs.rng(bits_a + bits_b)
+    N = 64
+    a = _rand_poly(g, N, bits_a)
+    b = _rand_poly(g, N, bits_b)
+    assert ring.negacyclic_fast(a, b) == ring.negacyclic_schoolbook(a, b)
+
+
+def test_fast_matches_kronecker_4096_at_key_switch_widths():
+    """N = 2^12 with 1,200 x 2,400-bit operands: a 3,600-bit product bound (takes ~15 s in Kronecker form)."""
+    g = fs.rng(10)
+    N = 4096
+    a = _rand_poly(g, N, 1200)
+    b = _rand_poly(g, N, 2400)
+    assert ring.negacyclic_fast(a, b) == ring.negacyclic_kronecker(a, b)
+
+
+def test_fast_binomial_closed_form_at_full_ring():
+    """N = 2^16: a full 1,200-bit polynomial times c X^i + d X^j (2,400-bit c, d) is the sum of two
+    negacyclic shifts, c X^i a + d X^j a; a wrong NTT length, root or CRT width fails it."""
+    g = fs.rng(11)
+    N = 1 << 16
+    a = _rand_poly(g, N, 1200)
+    c, d = _rand_poly(g, 2, 2400)
+    i, j = 1, N - 3
+    b = [0] * N
+    b[i], b[j] = c, d
+
+    def shift(v, k, m):  # m X^k v(X) in Z[X]/(X^N + 1)
+        return [m * (v[n - k] if n >= k else -v[n - k + N]) for n in range(N)]
+
+    want = [x + y for x, y in zip(shift(a, i, c), shift(a, j, d))]
+    assert ring.negacyclic_fast(a, b) == want

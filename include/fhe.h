@@ -246,14 +246,16 @@ int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int
 /* fhe_mult_relin_rescale for callers that cannot allocate device memory.
  * The paper has no counterpart; this exists for the library's users.
  * Some callers cannot call cudaMalloc (or any allocator) where they multiply:
- * code that runs while a stream is being captured into a CUDA graph, hosts
- * that forbid allocation after start-up, and plug-ins of other runtimes that
- * must not touch the process's device allocator.  This call takes no
+ * hosts that forbid allocation after start-up (real-time or embedded
+ * services, where an allocation may block or fail at a bad moment), and
+ * plug-ins of other runtimes that must not touch the process's device
+ * allocator (it belongs to the host runtime).  This call takes no
  * workspace and allocates nothing (no cudaMalloc/cudaFree, no allocator
  * callback).  Its scratch is one static device array of 32 MiB that every GPU
  * loading the library holds until the process exits; a call whose scratch
  * need (fhe_workspace_bytes(ctx, FHE_OP_MULT, a->logQ, a->cnum)) exceeds
- * 32 MiB is rejected with FHE_EINVAL before anything is enqueued.  The first
+ * 32 MiB is rejected with FHE_EINVAL before anything is enqueued, as are a
+ * BGV context and k < 1 (as for fhe_mult_relin_rescale).  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with the context's device current; make that first call before any stream
  * capture.  All calls share the one array and it keeps the last call's

@@ -2,10 +2,10 @@
 // that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or any allocator) at the point where
-// they multiply: code running while a stream is being captured into a CUDA
-// graph, real-time or embedded hosts that forbid allocation after start-up,
-// and plug-ins of other runtimes that must not touch the process's device
-// allocator.  This entry point gives them fhe_mult_relin_rescale without a
+// they multiply: real-time or embedded hosts that forbid allocation after
+// start-up (an allocation can block or fail at a bad moment), and plug-ins of
+// other runtimes that must not touch the process's device allocator (it
+// belongs to the host runtime, which accounts for every byte itself).  This entry point gives them fhe_mult_relin_rescale without a
 // caller workspace: its scratch is one file-scope device array of
 // kNoAllocScratchBytes (32 MiB), which every GPU that loads this library
 // holds until the process exits.  Nothing here allocates: no cudaMalloc, no
@@ -58,6 +58,11 @@ int fhe_mult_relin_rescale_noalloc(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* 
                                    void* stream) {
   if (!ctx || !a || !b || !out) {
     fhe::set_error("mult_relin_rescale_noalloc: null argument");
+    return FHE_EINVAL;
+  }
+  // the same argument errors as fhe_mult_relin_rescale, before any size or device question
+  if (ctx->prm.scheme != FHE_SCHEME_CKKS || k < 1) {
+    fhe::set_error("mult_relin_rescale_noalloc: CKKS only, k >= 1 (k = %d)", k);
     return FHE_EINVAL;
   }
   int dev = -1;

@@ -1,7 +1,7 @@
 """fhe_mult_relin_rescale_noalloc against fhe_mult_relin_rescale (needs a GB300).
 
 The no-allocation entry point serves callers that cannot allocate device
-memory where they multiply (inside a stream capture, allocation-free hosts,
+memory where they multiply (hosts that forbid allocation after start-up,
 plug-ins that must not touch the device allocator).  It must give the same
 ciphertexts, bit for bit, as the workspace entry point, call after call,
 even though every call reuses one static scratch array.  This file is named
@@ -69,4 +69,9 @@ def test_noalloc_rejects_work_beyond_the_static_scratch():
                                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == fhe.FHE_EINVAL
     assert b"static scratch" in fhe.lib.fhe_last_error()
+    # argument errors come first, as for fhe_mult_relin_rescale: k < 1 is rejected whatever the size
+    rc = fhe.lib.fhe_mult_relin_rescale_noalloc(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), 0, ctypes.byref(co),
+                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == fhe.FHE_EINVAL
+    assert b"k >= 1" in fhe.lib.fhe_last_error()
     ctx.close()

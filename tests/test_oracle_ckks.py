@@ -257,3 +257,75 @@ def test_rotation_below_the_top_level():
     out = ckks.rotate(ct, 3, rtk[3], prm.N, 97, prm.logP)
     dec = encode.decode(ckks.decrypt(s, out, 97), prm.N, 40, n)
     assert np.abs(dec - np.roll(z, -3)).max() < 2.0 ** -20
+
+
+def test_centred_representative_by_hand():
+    Q = 1 << 8
+    assert ckks.centred([0, 1, 127, 128, 129, 255, 256 + 3, -1], 8) == [0, 1, 127, -128, -127, -1, 3, -1]
+    assert all(-Q // 2 <= x < Q // 2 for x in ckks.centred(list(range(-300, 300)), 8))
+
+
+def test_rotation_adds_almost_no_error_at_scale_2_40():
+    """Key switching the centred representative: a rotation's slots are as accurate as the fresh
+    encryption's (N = 2^12, scale 2^40).  Key switching the [0, Q) representative instead makes the
+    key error's mean term Q/2 (1 + X + ... + X^(N-1)) e' / P, whose slots grow like N, and fails this."""
+    g, prm, s, pk, _, rtk = _rotation_setup(23, (1,), logN=12)
+    n = prm.N // 2
+    z = fs.unit_disk(g, n)
+    ct = _enc(g, prm, pk, encode.encode(z, prm.N, 40))
+    fresh = np.abs(encode.decode(ckks.decrypt(s, ct, prm.logQ), prm.N, 40, n) - z).max()
+    out = ckks.rotate(ct, 1, rtk[1], prm.N, prm.logQ, prm.logP)
+    rot = np.abs(encode.decode(ckks.decrypt(s, out, prm.logQ), prm.N, 40, n) - np.roll(z, -1)).max()
+    assert rot <= 1.5 * fresh and rot < 2.0 ** -22
+
+
+def test_conjugation_conjugates_every_slot():
+    g, prm, s, pk, _ = _setup(9, 120, 120, 24)
+    n = prm.N // 2
+    a = bigint.from_limbs(fs.uniform_limbs(g, (), prm.N, prm.logQ + prm.logP))
+    e = [int(x) for x in fs.gaussian(g, (), prm.N)]
+    ck = ckks.conjugation_key(prm, s, a, e)
+    # the key relation b' + a' s = e' + P s(X^-1) (mod P Q)
+    PQ = prm.P * prm.Q
+    lhs = ring.mod_poly(ring.add_poly(ck[0], ring.negacyclic_mul(ck[1], s)), PQ)
+    sc = ring.automorphism(s, 2 * prm.N - 1)
+    diff = ckks.centred([x - prm.P * y for x, y in zip(lhs, sc)], prm.logP + prm.logQ)
+    assert max(abs(d) for d in diff) <= fs.TAIL
+    z = fs.unit_disk(g, n)
+    ct = _enc(g, prm, pk, encode.encode(z, prm.N, 40))
+    out = ckks.conjugate(ct, ck, prm.N, prm.logQ, prm.logP)
+    dec = encode.decode(ckks.decrypt(s, out, prm.logQ), prm.N, 40, n)
+    assert np.abs(dec - np.conj(z)).max() < 2.0 ** -20
+    # X -> X^(2N-1) on the plaintext alone conjugates the slots (closed form of the canonical embedding)
+    m = encode.encode(z, prm.N, 40)
+    assert np.abs(encode.decode(ring.automorphism(m, 2 * prm.N - 1), prm.N, 40, n) - np.conj(z)).max() < 2.0 ** -30
+
+
+def test_imult_multiplies_slots_by_i():
+    g, prm, s, pk, _ = _setup(9, 120, 120, 25)
+    n = prm.N // 2
+    z = fs.unit_disk(g, n)
+    ct = _enc(g, prm, pk, encode.encode(z, prm.N, 40))
+    out = ckks.imult(ct, prm.N, prm.logQ)
+    dec = encode.decode(ckks.decrypt(s, out, prm.logQ), prm.N, 40, n)
+    assert np.abs(dec - 1j * z).max() < 2.0 ** -20
+    # i^2 = -1: imult twice is the negation, exactly (X^(N/2) X^(N/2) = X^N = -1)
+    assert ckks.imult(out, prm.N, prm.logQ) == ckks.negate(ct, prm.logQ)
+
+
+def test_mult_plain_multiplies_slots():
+    g, prm, s, pk, _ = _setup(9, 160, 160, 26)
+    n = prm.N // 2
+    z1, z2 = fs.unit_disk(g, n), fs.unit_disk(g, n)
+    ct = _enc(g, prm, pk, encode.encode(z1, prm.N, 40))
+    m2 = encode.encode(z2, prm.N, 30)
+    out = ckks.rescale(ckks.mult_plain(ct, m2, prm.logQ), 30, prm.logQ)
+    dec = encode.decode(ckks.decrypt(s, out, prm.logQ - 30), prm.N, 40, n)
+    assert np.abs(dec - z1 * z2).max() < 2.0 ** -20
+    # closed forms: the constant 1 is the identity, X^(N/2) is imult, -1 is the negation
+    one = [1] + [0] * (prm.N - 1)
+    assert ckks.mult_plain(ct, one, prm.logQ) == tuple(list(p) for p in ct)
+    half = [0] * prm.N
+    half[prm.N // 2] = 1
+    assert ckks.mult_plain(ct, half, prm.logQ) == ckks.imult(ct, prm.N, prm.logQ)
+    assert ckks.mult_plain(ct, [-1] + [0] * (prm.N - 1), prm.logQ) == ckks.negate(ct, prm.logQ)

@@ -62,12 +62,14 @@ extern "C" {
 
 /* Operation codes for fhe_workspace_bytes. */
 #define FHE_OP_MULT 1      /* fhe_mult_relin / fhe_mult_relin_rescale  */
-#define FHE_OP_ROTATE 2    /* fhe_rotate                               */
-#define FHE_OP_ENCRYPT 3   /* fhe_encrypt                              */
+#define FHE_OP_ROTATE 2    /* fhe_rotate, fhe_rotate_hoisted, fhe_conjugate */
+#define FHE_OP_ENCRYPT 3   /* fhe_encrypt, fhe_encrypt_inject          */
 #define FHE_OP_DECRYPT 4   /* fhe_decrypt                              */
-#define FHE_OP_KEYGEN 5    /* fhe_keygen, fhe_keygen_rotation (cnum 1) */
+#define FHE_OP_KEYGEN 5    /* key generation scratch (informational)   */
 #define FHE_OP_RING_MUL 6  /* fhe_ring_mul with logQ = max operand bits */
 #define FHE_OP_MULT_RAGGED 7 /* fhe_mult_relin_rescale_ragged, logQ = the largest level */
+#define FHE_OP_MULT_PLAIN 8  /* fhe_mult_plain                           */
+#define FHE_OP_ENCODE 9      /* fhe_ckks_encode / fhe_ckks_decode (logQ ignored) */
 
 typedef struct fhe_ctx fhe_ctx;
 
@@ -91,6 +93,10 @@ typedef struct {
   uint32_t t;         /* BGV: plaintext modulus, odd, 3 <= t < 2^31 (0 for CKKS)      */
   uint64_t bgv_q0;    /* BGV: odd, = 1 mod t                                         */
   uint64_t bgv_r;     /* BGV: odd, = 1 mod t, 2^8 < r < 2^62                           */
+  int32_t hamming_weight; /* secret of fhe_keygen: 0 = uniform ternary, h > 0 = exactly h
+                             nonzero coefficients in {-1, 1} (sparse secret, HEAAN's HWT)  */
+  double sigma;       /* error standard deviation of fhe_keygen / fhe_encrypt (0 = 3.2),
+                         rounded Gaussian cut at |e| <= floor(6 sigma), sigma <= 10        */
 } fhe_params;
 
 #define FHE_CRT_DIRECT 0     /* exact CRT sum with a rounded quotient (Halevi-Polyakov-Shoup);
@@ -108,6 +114,11 @@ typedef struct {
   int32_t logQ;   /* CKKS: this ciphertext's modulus 2^logQ (its level), <= the top.
                      BGV: the bit length of Q_level (must match `level`)             */
   int32_t level;  /* BGV: level l of the modulus Q_l = q0 r^l (ignored for CKKS)     */
+  double log_scale; /* CKKS: log2 of the scale Delta of the encrypted message.  The caller
+                       sets it on encryption; every operation writes its output's scale
+                       (mult: sum of the inputs', rescale by k: minus k, the rest: the
+                       input's) and fhe_add / fhe_sub reject operands whose scales differ
+                       by more than 1e-9 (FHE_ELEVEL).  Ignored for BGV.                   */
 } fhe_ct;
 
 /* Create a context for one ring size and modulus chain.  Computes the NTT
@@ -139,11 +150,25 @@ size_t fhe_ct_bytes(int logN, int logQ, int cnum);
  * (for FHE_OP_RING_MUL: logQ = the larger operand's bits).  0 on bad args. */
 size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum);
 
-/* Key generation (Sec. 6 "Cryptographic Key Management": sk, pk, rk).
+/* Key generation from a seed (Sec. 6 "Cryptographic Key Management": the secret
+ * key, the public key, the relinearisation key rk, rotation keys rtk_j and, for
+ * CKKS, the conjugation key ck).  Every random polynomial is drawn by the
+ * library's counter-based sampler (Philox4x32-10, Salmon et al. 2011) from
+ * `seed`; see fhe_sample for the streams and rules.  The secret is uniform
+ * ternary, or of Hamming weight params.hamming_weight; errors are rounded
+ * Gaussians of params.sigma; the uniform key parts are uniform mod 2^logQ and
+ * 2^(logP + logQ) (BGV: full 32-bit limbs, then reduced mod Q and P Q).
+ * rot_steps (host int[n_rot], may be NULL when n_rot = 0) lists the left
+ * rotations (negative = right) to make keys for.  The keys are then as
+ * fhe_keygen_inject and fhe_keygen_rotation make them from the same draws.
+ * Synchronous.  The same seed always gives the same keys: use a fresh,
+ * secret seed for every key set. */
+int fhe_keygen(fhe_ctx* ctx, uint64_t seed, const int* rot_steps, int n_rot);
+
+/* Key generation from caller-supplied random polynomials (host pointers), so
+ * that results can be reproduced outside the library.
  * BGV: the errors are multiplied by t, Q is the top chain modulus q0 r^L and
  * a_pk / a_ev are first reduced modulo Q and P Q (any limbs are accepted).
- * All random polynomials are supplied by the caller (host pointers), so that
- * results are reproducible:
  *   s     int8_t[N]            secret, coefficients in {-1, 0, 1}
  *   a_pk  uint32_t[Lq][N]      uniform mod Q,   Lq  = ceil(logQ/32)
  *   e_pk  int32_t[N]           small error
@@ -152,25 +177,67 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum);
  * Computes on the GPU pk = (-a_pk s + e_pk, a_pk) mod Q and
  * evk = (-a_ev s + e_ev + P s^2, a_ev) mod P*Q, and keeps them resident
  * (evk in NTT form over the key-switching primes).  Synchronous. */
-int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk, const uint32_t* a_ev,
-               const int32_t* e_ev);
+int fhe_keygen_inject(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk, const uint32_t* a_ev,
+                      const int32_t* e_ev);
 
 /* Rotation key for left rotation by `step` slots (Sec. 6 rtk; leftrotate):
  * rtk = (-a s + e + P s(X^g), a) mod P*Q with g = 5^step mod 2N.
- * a: host uint32_t[Lpq][N], e: host int32_t[N].  Requires fhe_keygen first.
- * Replaces an existing key for the same g.  Synchronous. */
+ * a: host uint32_t[Lpq][N], e: host int32_t[N].  Requires a key set first.
+ * Replaces an existing key for the same g.  CKKS only.  Synchronous. */
 int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e);
 
-/* Public-key encryption (encrypt_pairwise_upon, Sec. 6) of cnum plaintexts:
+/* Conjugation key (Sec. 6 ck, for conjugate_pairwise_into): the switching key
+ * of the automorphism X -> X^(2N-1), ck = (-a s + e + P s(X^-1), a) mod P*Q.
+ * Arguments as for fhe_keygen_rotation.  CKKS only.  Synchronous. */
+int fhe_keygen_conjugation(fhe_ctx* ctx, const uint32_t* a, const int32_t* e);
+
+/* Public-key encryption (encrypt_pairwise_upon, Sec. 6) of cnum plaintexts
+ * with the ephemeral v and errors e0, e1 of ciphertext c drawn by the
+ * library's sampler from (seed, c) (ternary v, rounded Gaussian e0, e1; see
+ * fhe_sample), then as fhe_encrypt_inject.  Never reuse a seed under one key:
+ * two encryptions with the same (seed, c) reveal their plaintext difference.
+ * Workspace: FHE_OP_ENCRYPT. */
+int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, uint64_t seed, fhe_ct* out, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* Public-key encryption with caller-supplied randomness:
  *   CKKS: out = (v pk_b + m + e0, v pk_a + e1) mod 2^out->logQ
  *   BGV:  out = (v pk_b + m + t e0, v pk_a + t e1) mod Q_{out->level}, pt canonical
  *         residues (m in [0, t) in limb 0)
  * pt: device uint32_t[cnum][L][N], each coefficient m mod 2^logQ (a signed
  * plaintext in two's complement); v: device int8_t[cnum][N] in {-1,0,1};
- * e0, e1: device int32_t[cnum][N].  out->data, out->cnum, out->logQ set by
- * the caller (logQ <= top).  FHE_ENOKEY before fhe_keygen. */
-int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1,
-                fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
+ * e0, e1: device int32_t[cnum][N].  out->data, out->cnum, out->logQ (and
+ * out->log_scale, the plaintext's scale) set by the caller (logQ <= top).
+ * FHE_ENOKEY before key generation. */
+int fhe_encrypt_inject(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1,
+                       fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
+
+/* The library's sampler on the host (no GPU needed): n coefficients of the
+ * stream (seed, tag0, tag1) that fhe_keygen and fhe_encrypt draw from.  Word j
+ * of a stream is component j mod 4 of Philox4x32-10 (Salmon et al., SC 2011)
+ * with counter (j/4 mod 2^32, j/2^34, tag0, tag1) and key (seed mod 2^32,
+ * seed / 2^32).  kind:
+ *   FHE_SAMPLE_UNIFORM   uint32_t[L][n] uniform mod 2^param (L = ceil(param/32));
+ *                        limb l of coefficient i is word l n + i, top limb masked
+ *   FHE_SAMPLE_TERNARY   int8_t[n], floor(3 w / 2^32) - 1
+ *   FHE_SAMPLE_HWT       int8_t[n] with exactly param nonzero coefficients in
+ *                        {-1, 1}: a partial Fisher-Yates shuffle over words 0..param-1
+ *                        (swap i, i + floor((n - i) w_i / 2^32)), signs from bit 0 of
+ *                        words param..2 param - 1 (odd = -1)
+ *   FHE_SAMPLE_GAUSSIAN  int32_t[n] rounded Gaussian of standard deviation sigma:
+ *                        the smallest k with w < T_k, T_k = floor(2^32 S_k / S_B),
+ *                        S_k the in-order double sums of exp(-k^2 / (2 sigma^2)) from
+ *                        k = -B, B = floor(6 sigma); B if there is none
+ * Tags used by the library (tag0): 1 secret, 2 / 3 public key a / e,
+ * 4 / 5 relinearisation key a / e, 6 / 7 switching key a / e with tag1 = its
+ * Galois element, 8 / 9 / 10 encryption v / e0 / e1 with tag1 = the
+ * ciphertext's index in the batch.  out: host memory.  FHE_EINVAL on a bad
+ * kind, parameter or n (1 <= n <= 2^24). */
+#define FHE_SAMPLE_UNIFORM 0
+#define FHE_SAMPLE_TERNARY 1
+#define FHE_SAMPLE_HWT 2
+#define FHE_SAMPLE_GAUSSIAN 3
+int fhe_sample(uint64_t seed, uint32_t tag0, uint32_t tag1, int kind, int n, int param, double sigma, void* out);
 
 /* Decryption (decrypt_pairwise_upon, Sec. 6): m = [b + a s]_Q with the centred
  * reduction of Sec. 5 ("if x > Q/2, x <- x - Q").  CKKS: written as L-limb two's
@@ -183,8 +250,11 @@ int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size
  * division (y + delta)/P, delta = t [(-y) t^-1]_P (centred), so delta = 0 mod t.
  * CKKS:
  *   (d0, d1, d2) = (b1 b2, a1 b2 + a2 b1, a1 a2) mod Q    (Karatsuba, Sec. 5)
- *   out = (d0, d1) + round(P^-1 (d2 evk_b, d2 evk_a) mod P Q)  (mod Q)
- * a, b: same cnum and logQ; out: same cnum and logQ, must not alias a or b. */
+ *   out = (d0, d1) + round(P^-1 (d2~ evk_b, d2~ evk_a) mod P Q)  (mod Q),
+ * d2~ the centred representative of d2 (logQ-bit two's complement).
+ * a, b: same logQ; b->cnum = a->cnum (pairwise mode) or 1 (broadcast mode: the
+ * one ciphertext b multiplies every ciphertext of a, Sec. 6 "Pairwise and
+ * Broadcast Modes"); out: a's cnum and logQ, must not alias a or b. */
 int fhe_mult_relin(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* ws, size_t ws_bytes,
                    void* stream);
 
@@ -216,13 +286,34 @@ int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream
  * out->level = in->level - 1, no aliasing. */
 int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
 
-/* Left rotation by `step` slots (leftrotate_broadcast_into, Sec. 6):
- * kappa_g(X) = X^g, g = 5^step mod 2N, then key switching with rtk_step:
- *   out = (kappa(b), 0) + round(P^-1 kappa(a) rtk mod P Q)  (mod Q).
- * FHE_ENOKEY without fhe_keygen_rotation(step).  out must not alias in. */
+/* Left rotation by `step` slots (leftrotate_broadcast_into, Sec. 6; negative
+ * steps rotate right): kappa_g(X) = X^g, g = 5^step mod 2N, then key switching
+ * with rtk_step:
+ *   out = (kappa(b), 0) + round(P^-1 kappa(a~) rtk mod P Q)  (mod Q),
+ * a~ the centred representative of a (its logQ-bit two's complement, in
+ * [-Q/2, Q/2)) and kappa taken over Z (coefficients negated, not reduced).
+ * FHE_ENOKEY without a key for g.  out must not alias in.  Workspace:
+ * FHE_OP_ROTATE (the same for one step and for fhe_rotate_hoisted). */
 int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
 
-/* Limb-domain operations (Sec. 5: add, subtract, negate without RNS). */
+/* The rotations of one ciphertext batch by nsteps steps (1..4096) at once:
+ * outs[s] (host array of nsteps ciphertext descriptors, device data) receives
+ * fhe_rotate(in, steps[s]), bit for bit.  The key-switch input is lifted and
+ * transformed once for all steps; each automorphism is then applied as a
+ * permutation of the transform (hoisted rotations).  Outputs must not alias
+ * the input or each other. */
+int fhe_rotate_hoisted(fhe_ctx* ctx, const fhe_ct* in, const int* steps, int nsteps, fhe_ct* const* outs, void* ws,
+                       size_t ws_bytes, void* stream);
+
+/* Complex conjugation of the slots (conjugate_pairwise_into, Sec. 6): the
+ * automorphism X -> X^(2N-1) with key switching by the conjugation key, in the
+ * form of fhe_rotate.  FHE_ENOKEY without a conjugation key (fhe_keygen makes
+ * one; fhe_keygen_conjugation injects one).  Workspace: FHE_OP_ROTATE. */
+int fhe_conjugate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Limb-domain operations (Sec. 5: add, subtract, negate without RNS).  For
+ * fhe_add / fhe_sub (CKKS), b->cnum may be 1 (broadcast mode: b is added to or
+ * subtracted from every ciphertext of a; out must not alias b). */
 int fhe_add(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream);
 int fhe_sub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream);
 int fhe_negate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
@@ -234,6 +325,29 @@ int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void*
  * value * 2^shift (mod 2^logQ), i.e. every slot gains value 2^shift / Delta.
  * CKKS only; 0 <= shift < logQ; out may alias in. */
 int fhe_add_const(fhe_ctx* ctx, const fhe_ct* in, int64_t value, int shift, fhe_ct* out, void* stream);
+
+/* addconst_pairwise_into (Sec. 6): ciphertext c gains values[c] * 2^shift at
+ * coefficient 0 of b (values: device int64_t[cnum]).  CKKS only; out may alias in. */
+int fhe_add_const_vec(fhe_ctx* ctx, const fhe_ct* in, const int64_t* values, int shift, fhe_ct* out, void* stream);
+
+/* imult_pairwise_into (Sec. 6): multiplication of every slot by the imaginary
+ * unit, i.e. of both polynomials by X^(N/2) (X^(N/2) evaluates to i at every
+ * slot's root 5^j, 5^j = 1 mod 4): coefficient j moves to j + N/2 and is
+ * negated when it wraps past X^N = -1.  No key and no noise growth.  CKKS
+ * only; out must not alias in. */
+int fhe_imult(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream);
+
+/* multconstvec_pairwise_into (Sec. 6): multiplication by encoded plaintext
+ * polynomials, out = (b m, a m) mod 2^logQ.  pt: device uint32_t[pt_cnum][L][N],
+ * each coefficient m mod 2^logQ (two's complement for negative values);
+ * pt_cnum = cnum pairs plaintext c with ciphertext c, pt_cnum = 1 broadcasts
+ * one plaintext (multconst_broadcast_into with a vector constant).  The
+ * product is exact in Z[X]/(X^N + 1) before the reduction (one ring product
+ * of each polynomial, Sec. 5 pipeline).  out->log_scale = in's + pt_log_scale
+ * (follow with fhe_rescale).  CKKS only; out must not alias in.
+ * Workspace: FHE_OP_MULT_PLAIN. */
+int fhe_mult_plain(fhe_ctx* ctx, const fhe_ct* in, const uint32_t* pt, int pt_cnum, double pt_log_scale, fhe_ct* out,
+                   void* ws, size_t ws_bytes, void* stream);
 
 /* The big-integer negacyclic multiplier of Sec. 5 on its own:
  *   out = a * b mod 2^logOut in Z[X]/(X^N + 1),
@@ -287,6 +401,46 @@ int fhe_profile_reset(fhe_ctx* ctx, int enable);
  * was enabled) the summed event-measured device time in milliseconds.
  * Synchronises on the recorded events.  FHE_EINVAL for a bad class. */
 int fhe_profile_read(fhe_ctx* ctx, int kclass, int64_t* launches, double* ms);
+
+/* CKKS encoding on the GPU (Sec. 2 "Fast Fourier Transform"; HEAAN slots):
+ * z: device complex double [cnum][N/2] (real, imaginary interleaved), full
+ * packing; pt: device uint32_t[cnum][ceil(logQ/32)][N] receives m with
+ * m(zeta^(5^j)) ~= 2^log_scale z_j, zeta = exp(i pi / N), i.e. the integer
+ * nearest (ties to even) to the inverse canonical embedding, as logQ-bit two's
+ * complement.  Requires 2^log_scale max|z_j| < 2^61 (0 <= log_scale <= 62).
+ * Double-precision DFTs: coefficients can differ by one from another
+ * implementation's rounding where the exact value lies within about 2^-40 of a
+ * half-integer.  Workspace: FHE_OP_ENCODE (cnum). */
+int fhe_ckks_encode(fhe_ctx* ctx, const double* z, int cnum, int log_scale, int logQ, uint32_t* pt, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* CKKS decoding on the GPU: pt device uint32_t[cnum][ceil(logQ/32)][N] holding
+ * signed plaintexts in two's complement (as fhe_decrypt writes them);
+ * z: device complex double [cnum][N/2] receives m(zeta^(5^j)) / 2^log_scale.
+ * Workspace: FHE_OP_ENCODE (cnum). */
+int fhe_ckks_decode(fhe_ctx* ctx, const uint32_t* pt, int cnum, int logQ, double log_scale, double* z, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* BGV slot batching (Sec. 2 "Chinese Remainder Theorem", polynomial CRT):
+ * for a prime t = 1 (mod 2N) (N <= 2^15), slot k of a plaintext m in
+ * Z_t[X]/(X^N + 1) is m(psi^(2k+1)) mod t, psi = g^((t-1)/(2N)) with g the
+ * smallest primitive root mod t; slot-wise products are ring products.
+ * fhe_bgv_encode: slots device uint32_t[cnum][N] (values mod t) -> the
+ * coefficients of m in [0, t), ciphertext c's at pt + c * pt_stride (pass
+ * L N to write limb 0 of an fhe_encrypt input whose other limbs are zero).
+ * fhe_bgv_decode: the inverse, from coefficients at pt + c * pt_stride (as
+ * fhe_decrypt writes them for BGV: pt_stride = N).  FHE_EINVAL when t is not
+ * such a prime. */
+int fhe_bgv_encode(fhe_ctx* ctx, const uint32_t* slots, int cnum, uint32_t* pt, size_t pt_stride, void* stream);
+int fhe_bgv_decode(fhe_ctx* ctx, const uint32_t* pt, size_t pt_stride, int cnum, uint32_t* slots, void* stream);
+
+/* Self-test of failure detection (no counterpart in the paper): launches one
+ * thread that waits on a shared-memory barrier nothing arrives on, polling at
+ * most `tries` (1..100000) times with a 1 us suspend hint, then records the
+ * timeout in the device status word and returns, exactly as a pipeline wait of
+ * the tensor-core kernels does when it gives up.  The next fhe_sync returns
+ * FHE_ETIMEOUT (and clears the word); the context stays usable. */
+int fhe_selftest_wait_timeout(int tries, void* stream);
 
 /* Number of NTT primes the library uses for a ring product whose exact
  * result is bounded by 2^bound_bits in absolute value (one spare prime for

@@ -147,3 +147,55 @@ def plaintext_power(m, k: int, N: int, t: int) -> list[int]:
     for _ in range(k):
         x = ring.mod_poly(ring.negacyclic_mul(x, x), t)
     return x
+
+
+def primitive_root(t: int) -> int:
+    """The smallest generator of the multiplicative group mod the prime t."""
+    r, fac, d = t - 1, [], 2
+    while d * d <= r:
+        if r % d == 0:
+            fac.append(d)
+            while r % d == 0:
+                r //= d
+        d += 1
+    if r > 1:
+        fac.append(r)
+    g = 2
+    while any(pow(g, (t - 1) // p, t) == 1 for p in fac):
+        g += 1
+    return g
+
+
+def slot_root(N: int, t: int) -> int:
+    """psi = g^((t-1)/(2N)): a primitive 2N-th root of unity mod t (needs t = 1 mod 2N)."""
+    assert (t - 1) % (2 * N) == 0
+    return pow(primitive_root(t), (t - 1) // (2 * N), t)
+
+
+def slot_decode(m, N: int, t: int) -> list[int]:
+    """Slots of a plaintext (Sec. 2 polynomial CRT): slot k = m(psi^(2k+1)) mod t, by the direct sum."""
+    psi = slot_root(N, t)
+    out = []
+    for k in range(N):
+        x = pow(psi, 2 * k + 1, t)
+        acc, p = 0, 1
+        for j in range(N):
+            acc = (acc + int(m[j]) * p) % t
+            p = p * x % t
+        out.append(acc)
+    return out
+
+
+def slot_encode(slots, N: int, t: int) -> list[int]:
+    """The plaintext whose slots are `slots`: m_j = N^-1 sum_k slots_k psi^(-(2k+1) j) mod t (inverse of the
+    evaluation at the N distinct roots psi^(2k+1) of X^N + 1)."""
+    psi_inv = pow(slot_root(N, t), t - 2, t)
+    n_inv = pow(N, t - 2, t)
+    out = []
+    for j in range(N):
+        acc = 0
+        for k in range(N):
+            acc = (acc + int(slots[k]) * pow(psi_inv, (2 * k + 1) * j, t)) % t
+        out.append(acc * n_inv % t)
+    return out
+

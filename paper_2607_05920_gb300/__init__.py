@@ -46,17 +46,24 @@ FHE_OP_DECRYPT = 4
 FHE_OP_KEYGEN = 5
 FHE_OP_RING_MUL = 6
 FHE_OP_MULT_RAGGED = 7
+FHE_OP_MULT_PLAIN = 8
+FHE_OP_ENCODE = 9
+FHE_SAMPLE_UNIFORM = 0
+FHE_SAMPLE_TERNARY = 1
+FHE_SAMPLE_HWT = 2
+FHE_SAMPLE_GAUSSIAN = 3
 
 
 class FheParams(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("logN", ctypes.c_int32), ("logQ", ctypes.c_int32),
                 ("logP", ctypes.c_int32), ("crt", ctypes.c_int32), ("bgv_levels", ctypes.c_int32),
-                ("t", ctypes.c_uint32), ("bgv_q0", ctypes.c_uint64), ("bgv_r", ctypes.c_uint64)]
+                ("t", ctypes.c_uint32), ("bgv_q0", ctypes.c_uint64), ("bgv_r", ctypes.c_uint64),
+                ("hamming_weight", ctypes.c_int32), ("sigma", ctypes.c_double)]
 
 
 class FheCt(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("cnum", ctypes.c_int32), ("logQ", ctypes.c_int32),
-                ("level", ctypes.c_int32)]
+                ("level", ctypes.c_int32), ("log_scale", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -74,9 +81,13 @@ SIGNATURES = {
     "fhe_sync": (_I, [_P]),
     "fhe_ct_bytes": (_SZ, [_I, _I, _I]),
     "fhe_workspace_bytes": (_SZ, [_P, _I, _I, _I]),
-    "fhe_keygen": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fhe_keygen": (_I, [_P, ctypes.c_uint64, _P, _I]),
+    "fhe_keygen_inject": (_I, [_P, _P, _P, _P, _P, _P]),
     "fhe_keygen_rotation": (_I, [_P, _I, _P, _P]),
-    "fhe_encrypt": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_keygen_conjugation": (_I, [_P, _P, _P]),
+    "fhe_encrypt": (_I, [_P, _P, ctypes.c_uint64, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_encrypt_inject": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_sample": (_I, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _I, _I, _I, ctypes.c_double, _P]),
     "fhe_decrypt": (_I, [_P, ctypes.POINTER(FheCt), _P, _P, _SZ, _P]),
     "fhe_mult_relin": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P, _SZ, _P]),
     "fhe_mult_relin_rescale": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P,
@@ -85,13 +96,23 @@ SIGNATURES = {
     "fhe_mult_relin_rescale_ragged": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _I, _P, _SZ, _P]),
     "fhe_moddown": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_rotate": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P, _SZ, _P]),
+    "fhe_rotate_hoisted": (_I, [_P, ctypes.POINTER(FheCt), _P, _I, _P, _P, _SZ, _P]),
+    "fhe_conjugate": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P, _SZ, _P]),
     "fhe_add": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_sub": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_negate": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_mult_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int32, ctypes.POINTER(FheCt), _P]),
     "fhe_ring_mul": (_I, [_P, _P, _I, _P, _I, _I, _P, _I, _P, _SZ, _P]),
     "fhe_add_const": (_I, [_P, ctypes.POINTER(FheCt), ctypes.c_int64, _I, ctypes.POINTER(FheCt), _P]),
+    "fhe_add_const_vec": (_I, [_P, ctypes.POINTER(FheCt), _P, _I, ctypes.POINTER(FheCt), _P]),
+    "fhe_imult": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
+    "fhe_mult_plain": (_I, [_P, ctypes.POINTER(FheCt), _P, _I, ctypes.c_double, ctypes.POINTER(FheCt), _P, _SZ, _P]),
     "fhe_primes_for_bound": (_I, [_I]),
+    "fhe_selftest_wait_timeout": (_I, [_I, _P]),
+    "fhe_ckks_encode": (_I, [_P, _P, _I, _I, _I, _P, _P, _SZ, _P]),
+    "fhe_ckks_decode": (_I, [_P, _P, _I, _I, ctypes.c_double, _P, _P, _SZ, _P]),
+    "fhe_bgv_encode": (_I, [_P, _P, _I, _P, _SZ, _P]),
+    "fhe_bgv_decode": (_I, [_P, _P, _SZ, _I, _P, _P]),
     "fhe_mult_relin_rescale_noalloc": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I,
                                             ctypes.POINTER(FheCt), _P]),
     "fhe_profile_reset": (_I, [_P, _I]),
@@ -141,6 +162,7 @@ class Ciphertext:
     data: "object"
     logQ: int
     level: int = 0
+    log_scale: float = 0.0
 
     @property
     def cnum(self) -> int:
@@ -149,7 +171,7 @@ class Ciphertext:
     def c(self) -> FheCt:
         if not self.data.is_contiguous():
             raise ValueError("ciphertext tensor must be contiguous (the C ABI reads a dense [cnum][2][L][N] block)")
-        return FheCt(self.data.data_ptr(), self.cnum, self.logQ, self.level)
+        return FheCt(self.data.data_ptr(), self.cnum, self.logQ, self.level, float(self.log_scale))
 
 
 def _stream():
@@ -167,7 +189,8 @@ class Context:
     """One ring size and modulus chain; owns tables and keys (allocated through torch)."""
 
     def __init__(self, logN: int, logQ: int, logP: int, crt: int = FHE_CRT_DIRECT, scheme: int = FHE_SCHEME_CKKS,
-                 t: int = 0, bgv_q0: int = 0, bgv_r: int = 0, bgv_levels: int = 0):
+                 t: int = 0, bgv_q0: int = 0, bgv_r: int = 0, bgv_levels: int = 0, hamming_weight: int = 0,
+                 sigma: float = 0.0):
         import torch
 
         self.logN, self.logQ, self.logP = int(logN), int(logQ), int(logP)
@@ -187,7 +210,7 @@ class Context:
         self._alloc_cb = ALLOC_FN(_alloc)
         self._free_cb = FREE_FN(_free)
         prm = FheParams(int(scheme), self.logN, self.logQ, self.logP, int(crt), int(bgv_levels), int(t), int(bgv_q0),
-                        int(bgv_r))
+                        int(bgv_r), int(hamming_weight), float(sigma))
         self.crt = int(crt)
         self.scheme = int(scheme)
         self.t, self.bgv_q0, self.bgv_r, self.bgv_levels = int(t), int(bgv_q0), int(bgv_r), int(bgv_levels)
@@ -229,29 +252,44 @@ class Context:
         """Bit length of Q_level = q0 r^level (BGV)."""
         return (self.bgv_q0 * self.bgv_r ** int(level)).bit_length()
 
-    def empty_ct(self, cnum: int, logQ: int, level: int = 0) -> Ciphertext:
+    def empty_ct(self, cnum: int, logQ: int, level: int = 0, log_scale: float = 0.0) -> Ciphertext:
         t = self._torch.empty((int(cnum), 2, limbs(logQ), self.N), dtype=self._torch.int32, device=self.device)
-        return Ciphertext(t, int(logQ), int(level))
+        return Ciphertext(t, int(logQ), int(level), float(log_scale))
 
     def empty_level(self, cnum: int, level: int) -> Ciphertext:
         """An uninitialised BGV ciphertext batch at `level`."""
         return self.empty_ct(cnum, self.bgv_bits(level), level)
 
     # ------------------------------------------------------------------ keys
-    def keygen(self, s, a_pk, e_pk, a_ev, e_ev) -> None:
-        fhe_keygen(self, s, a_pk, e_pk, a_ev, e_ev)
+    def keygen(self, seed: int, rot_steps=()) -> None:
+        fhe_keygen(self, seed, rot_steps)
+
+    def keygen_inject(self, s, a_pk, e_pk, a_ev, e_ev) -> None:
+        fhe_keygen_inject(self, s, a_pk, e_pk, a_ev, e_ev)
 
     def keygen_rotation(self, step: int, a, e) -> None:
         fhe_keygen_rotation(self, step, a, e)
 
+    def keygen_conjugation(self, a, e) -> None:
+        fhe_keygen_conjugation(self, a, e)
+
     # ------------------------------------------------------------ operations
-    def encrypt(self, pt, v, e0, e1, logQ: int | None = None, level: int | None = None) -> Ciphertext:
+    def _enc_out(self, cnum, logQ, level, log_scale):
         if self.scheme == FHE_SCHEME_BGV:
             lv = self.bgv_levels if level is None else int(level)
-            out = self.empty_level(pt.shape[0], lv)
-        else:
-            out = self.empty_ct(pt.shape[0], self.logQ if logQ is None else logQ)
-        fhe_encrypt(self, pt, v, e0, e1, out)
+            return self.empty_level(cnum, lv)
+        return self.empty_ct(cnum, self.logQ if logQ is None else logQ, log_scale=log_scale)
+
+    def encrypt(self, pt, seed: int, logQ: int | None = None, level: int | None = None,
+                log_scale: float = 0.0) -> Ciphertext:
+        out = self._enc_out(pt.shape[0], logQ, level, log_scale)
+        fhe_encrypt(self, pt, seed, out)
+        return out
+
+    def encrypt_inject(self, pt, v, e0, e1, logQ: int | None = None, level: int | None = None,
+                       log_scale: float = 0.0) -> Ciphertext:
+        out = self._enc_out(pt.shape[0], logQ, level, log_scale)
+        fhe_encrypt_inject(self, pt, v, e0, e1, out)
         return out
 
     def decrypt(self, ct: Ciphertext):
@@ -294,6 +332,16 @@ class Context:
         fhe_rotate(self, ct, step, out)
         return out
 
+    def rotate_hoisted(self, ct: Ciphertext, steps) -> list:
+        outs = [self.empty_ct(ct.cnum, ct.logQ) for _ in steps]
+        fhe_rotate_hoisted(self, ct, steps, outs)
+        return outs
+
+    def conjugate(self, ct: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(ct.cnum, ct.logQ)
+        fhe_conjugate(self, ct, out)
+        return out
+
     def add(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
         out = self.empty_ct(a.cnum, a.logQ, a.level)
         fhe_add(self, a, b, out)
@@ -314,6 +362,21 @@ class Context:
         fhe_mult_const(self, a, c, out)
         return out
 
+    def imult(self, a: Ciphertext) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_imult(self, a, out)
+        return out
+
+    def mult_plain(self, a: Ciphertext, pt, pt_log_scale: float = 0.0) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_mult_plain(self, a, pt, pt_log_scale, out)
+        return out
+
+    def add_const_vec(self, a: Ciphertext, values, shift: int) -> Ciphertext:
+        out = self.empty_ct(a.cnum, a.logQ)
+        fhe_add_const_vec(self, a, values, shift, out)
+        return out
+
     def ring_mul(self, a, b, logOut: int):
         cnum = a.shape[0]
         out = self._torch.empty((cnum, limbs(logOut), self.N), dtype=self._torch.int32, device=self.device)
@@ -322,15 +385,21 @@ class Context:
 
 
 # ------------------------------------------------ C-ABI-named thin wrappers
-def fhe_keygen(ctx: Context, s, a_pk, e_pk, a_ev, e_ev) -> None:
+def fhe_keygen(ctx: Context, seed: int, rot_steps=()) -> None:
+    steps = np.ascontiguousarray(np.asarray(list(rot_steps), dtype=np.int32))
+    _check(lib.fhe_keygen(ctx.handle, int(seed) & (2 ** 64 - 1), steps.ctypes.data if steps.size else None,
+                          int(steps.size)), "fhe_keygen")
+
+
+def fhe_keygen_inject(ctx: Context, s, a_pk, e_pk, a_ev, e_ev) -> None:
     N = ctx.N
     s = _host(s, np.int8).reshape(N)
     a_pk = _host(a_pk, np.uint32).reshape(limbs(ctx.logQ), N)
     e_pk = _host(e_pk, np.int32).reshape(N)
     a_ev = _host(a_ev, np.uint32).reshape(limbs(ctx.logQ + ctx.logP), N)
     e_ev = _host(e_ev, np.int32).reshape(N)
-    _check(lib.fhe_keygen(ctx.handle, s.ctypes.data, a_pk.ctypes.data, e_pk.ctypes.data, a_ev.ctypes.data,
-                          e_ev.ctypes.data), "fhe_keygen")
+    _check(lib.fhe_keygen_inject(ctx.handle, s.ctypes.data, a_pk.ctypes.data, e_pk.ctypes.data, a_ev.ctypes.data,
+                                 e_ev.ctypes.data), "fhe_keygen_inject")
 
 
 def fhe_keygen_rotation(ctx: Context, step: int, a, e) -> None:
@@ -338,6 +407,27 @@ def fhe_keygen_rotation(ctx: Context, step: int, a, e) -> None:
     a = _host(a, np.uint32).reshape(limbs(ctx.logQ + ctx.logP), N)
     e = _host(e, np.int32).reshape(N)
     _check(lib.fhe_keygen_rotation(ctx.handle, int(step), a.ctypes.data, e.ctypes.data), "fhe_keygen_rotation")
+
+
+def fhe_keygen_conjugation(ctx: Context, a, e) -> None:
+    N = ctx.N
+    a = _host(a, np.uint32).reshape(limbs(ctx.logQ + ctx.logP), N)
+    e = _host(e, np.int32).reshape(N)
+    _check(lib.fhe_keygen_conjugation(ctx.handle, a.ctypes.data, e.ctypes.data), "fhe_keygen_conjugation")
+
+
+def fhe_sample(seed: int, tag0: int, tag1: int, kind: int, n: int, param: int = 0, sigma: float = 3.2) -> np.ndarray:
+    """The library's host sampler (see include/fhe.h): uniform limbs (L, n) uint32, ternary / HWT int8 (n,),
+    Gaussian int32 (n,)."""
+    if kind == FHE_SAMPLE_UNIFORM:
+        out = np.zeros((limbs(param), n), dtype=np.uint32)
+    elif kind in (FHE_SAMPLE_TERNARY, FHE_SAMPLE_HWT):
+        out = np.zeros(n, dtype=np.int8)
+    else:
+        out = np.zeros(n, dtype=np.int32)
+    _check(lib.fhe_sample(int(seed) & (2 ** 64 - 1), int(tag0), int(tag1), int(kind), int(n), int(param),
+                          float(sigma), out.ctypes.data), "fhe_sample")
+    return out
 
 
 def _dev(t, dtype, shape):
@@ -348,15 +438,25 @@ def _dev(t, dtype, shape):
     return t.data_ptr()
 
 
-def fhe_encrypt(ctx: Context, pt, v, e0, e1, out: Ciphertext) -> None:
+def fhe_encrypt(ctx: Context, pt, seed: int, out: Ciphertext) -> None:
     import torch
 
     cnum, L, N = out.cnum, limbs(out.logQ), ctx.N
     ws = ctx.workspace(FHE_OP_ENCRYPT, ctx.logQ, cnum)
     oc = out.c()
-    _check(lib.fhe_encrypt(ctx.handle, _dev(pt, torch.int32, (cnum, L, N)), _dev(v, torch.int8, (cnum, N)),
-                           _dev(e0, torch.int32, (cnum, N)), _dev(e1, torch.int32, (cnum, N)), ctypes.byref(oc),
-                           ws.data_ptr(), ws.numel(), _stream()), "fhe_encrypt")
+    _check(lib.fhe_encrypt(ctx.handle, _dev(pt, torch.int32, (cnum, L, N)), int(seed) & (2 ** 64 - 1),
+                           ctypes.byref(oc), ws.data_ptr(), ws.numel(), _stream()), "fhe_encrypt")
+
+
+def fhe_encrypt_inject(ctx: Context, pt, v, e0, e1, out: Ciphertext) -> None:
+    import torch
+
+    cnum, L, N = out.cnum, limbs(out.logQ), ctx.N
+    ws = ctx.workspace(FHE_OP_ENCRYPT, ctx.logQ, cnum)
+    oc = out.c()
+    _check(lib.fhe_encrypt_inject(ctx.handle, _dev(pt, torch.int32, (cnum, L, N)), _dev(v, torch.int8, (cnum, N)),
+                                  _dev(e0, torch.int32, (cnum, N)), _dev(e1, torch.int32, (cnum, N)),
+                                  ctypes.byref(oc), ws.data_ptr(), ws.numel(), _stream()), "fhe_encrypt_inject")
 
 
 def fhe_decrypt(ctx: Context, ct: Ciphertext, out) -> None:
@@ -374,6 +474,7 @@ def fhe_mult_relin(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) 
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_mult_relin(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), ws.data_ptr(),
                               ws.numel(), _stream()), "fhe_mult_relin")
+    out.log_scale = co.log_scale
 
 
 def fhe_mult_relin_rescale(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, out: Ciphertext) -> None:
@@ -381,6 +482,7 @@ def fhe_mult_relin_rescale(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, o
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_mult_relin_rescale(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k), ctypes.byref(co),
                                       ws.data_ptr(), ws.numel(), _stream()), "fhe_mult_relin_rescale")
+    out.log_scale = co.log_scale
 
 
 def fhe_mult_relin_rescale_noalloc(ctx: Context, a: Ciphertext, b: Ciphertext, k: int, out: Ciphertext) -> None:
@@ -388,6 +490,7 @@ def fhe_mult_relin_rescale_noalloc(ctx: Context, a: Ciphertext, b: Ciphertext, k
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_mult_relin_rescale_noalloc(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), int(k),
                                               ctypes.byref(co), _stream()), "fhe_mult_relin_rescale_noalloc")
+    out.log_scale = co.log_scale
 
 
 def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: int, k: int, ws=None) -> None:
@@ -407,11 +510,13 @@ def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: 
 def fhe_rescale(ctx: Context, ct: Ciphertext, k: int, out: Ciphertext) -> None:
     ci, co = ct.c(), out.c()
     _check(lib.fhe_rescale(ctx.handle, ctypes.byref(ci), int(k), ctypes.byref(co), _stream()), "fhe_rescale")
+    out.log_scale = co.log_scale
 
 
 def fhe_moddown(ctx: Context, ct: Ciphertext, out: Ciphertext) -> None:
     ci, co = ct.c(), out.c()
     _check(lib.fhe_moddown(ctx.handle, ctypes.byref(ci), ctypes.byref(co), _stream()), "fhe_moddown")
+    out.log_scale = co.log_scale
 
 
 def fhe_rotate(ctx: Context, ct: Ciphertext, step: int, out: Ciphertext, ws=None) -> None:
@@ -420,32 +525,89 @@ def fhe_rotate(ctx: Context, ct: Ciphertext, step: int, out: Ciphertext, ws=None
     ci, co = ct.c(), out.c()
     _check(lib.fhe_rotate(ctx.handle, ctypes.byref(ci), int(step), ctypes.byref(co), ws.data_ptr(), ws.numel(),
                           _stream()), "fhe_rotate")
+    out.log_scale = co.log_scale
+
+
+def fhe_rotate_hoisted(ctx: Context, ct: Ciphertext, steps, outs, ws=None) -> None:
+    if ws is None:
+        ws = ctx.workspace(FHE_OP_ROTATE, ct.logQ, ct.cnum)
+    st = np.ascontiguousarray(np.asarray(list(steps), dtype=np.int32))
+    cs = [o.c() for o in outs]
+    arr = (ctypes.POINTER(FheCt) * len(cs))(*[ctypes.pointer(c) for c in cs])
+    ci = ct.c()
+    _check(lib.fhe_rotate_hoisted(ctx.handle, ctypes.byref(ci), st.ctypes.data, int(st.size), arr, ws.data_ptr(),
+                                  ws.numel(), _stream()), "fhe_rotate_hoisted")
+    for o, c in zip(outs, cs):
+        o.log_scale = c.log_scale
+
+
+def fhe_conjugate(ctx: Context, ct: Ciphertext, out: Ciphertext, ws=None) -> None:
+    if ws is None:
+        ws = ctx.workspace(FHE_OP_ROTATE, ct.logQ, ct.cnum)
+    ci, co = ct.c(), out.c()
+    _check(lib.fhe_conjugate(ctx.handle, ctypes.byref(ci), ctypes.byref(co), ws.data_ptr(), ws.numel(), _stream()),
+           "fhe_conjugate")
+    out.log_scale = co.log_scale
 
 
 def fhe_add(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_add(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()), "fhe_add")
+    out.log_scale = co.log_scale
 
 
 def fhe_sub(ctx: Context, a: Ciphertext, b: Ciphertext, out: Ciphertext) -> None:
     ca, cb, co = a.c(), b.c(), out.c()
     _check(lib.fhe_sub(ctx.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()), "fhe_sub")
+    out.log_scale = co.log_scale
 
 
 def fhe_negate(ctx: Context, a: Ciphertext, out: Ciphertext) -> None:
     ca, co = a.c(), out.c()
     _check(lib.fhe_negate(ctx.handle, ctypes.byref(ca), ctypes.byref(co), _stream()), "fhe_negate")
+    out.log_scale = co.log_scale
 
 
 def fhe_mult_const(ctx: Context, a: Ciphertext, c: int, out: Ciphertext) -> None:
     ca, co = a.c(), out.c()
     _check(lib.fhe_mult_const(ctx.handle, ctypes.byref(ca), int(c), ctypes.byref(co), _stream()), "fhe_mult_const")
+    out.log_scale = co.log_scale
 
 
 def fhe_add_const(ctx: Context, a: Ciphertext, value: int, shift: int, out: Ciphertext) -> None:
     ca, co = a.c(), out.c()
     _check(lib.fhe_add_const(ctx.handle, ctypes.byref(ca), int(value), int(shift), ctypes.byref(co), _stream()),
            "fhe_add_const")
+    out.log_scale = co.log_scale
+
+
+def fhe_add_const_vec(ctx: Context, a: Ciphertext, values, shift: int, out: Ciphertext) -> None:
+    """values: a CUDA int64 tensor (cnum,)."""
+    import torch
+
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_add_const_vec(ctx.handle, ctypes.byref(ca), _dev(values, torch.int64, (a.cnum,)), int(shift),
+                                 ctypes.byref(co), _stream()), "fhe_add_const_vec")
+    out.log_scale = co.log_scale
+
+
+def fhe_imult(ctx: Context, a: Ciphertext, out: Ciphertext) -> None:
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_imult(ctx.handle, ctypes.byref(ca), ctypes.byref(co), _stream()), "fhe_imult")
+    out.log_scale = co.log_scale
+
+
+def fhe_mult_plain(ctx: Context, a: Ciphertext, pt, pt_log_scale: float, out: Ciphertext) -> None:
+    """pt: a CUDA int32 tensor (pt_cnum, L, N) of uint32 limbs, pt_cnum = cnum or 1 (broadcast)."""
+    import torch
+
+    pc = int(pt.shape[0])
+    ws = ctx.workspace(FHE_OP_MULT_PLAIN, a.logQ, a.cnum)
+    ca, co = a.c(), out.c()
+    _check(lib.fhe_mult_plain(ctx.handle, ctypes.byref(ca), _dev(pt, torch.int32, (pc, limbs(a.logQ), ctx.N)), pc,
+                              float(pt_log_scale), ctypes.byref(co), ws.data_ptr(), ws.numel(), _stream()),
+           "fhe_mult_plain")
+    out.log_scale = co.log_scale
 
 
 def fhe_ring_mul(ctx: Context, a, b, logOut: int, out) -> None:
@@ -458,6 +620,54 @@ def fhe_ring_mul(ctx: Context, a, b, logOut: int, out) -> None:
                             _dev(b, torch.int32, (cnum, Lb, N)), int(Lb), int(logOut),
                             _dev(out, torch.int32, (cnum, limbs(logOut), N)), int(cnum), ws.data_ptr(), ws.numel(),
                             _stream()), "fhe_ring_mul")
+
+
+def fhe_ckks_encode(ctx: Context, z, log_scale: int, logQ: int):
+    """z: CUDA complex128 tensor (cnum, N/2) -> plaintext limbs (cnum, ceil(logQ/32), N) int32."""
+    import torch
+
+    cnum = int(z.shape[0])
+    pt = torch.empty((cnum, limbs(logQ), ctx.N), dtype=torch.int32, device=ctx.device)
+    ws = ctx.workspace(FHE_OP_ENCODE, 1, cnum)
+    _check(lib.fhe_ckks_encode(ctx.handle, _dev(z, torch.complex128, (cnum, ctx.N // 2)), cnum, int(log_scale),
+                               int(logQ), pt.data_ptr(), ws.data_ptr(), ws.numel(), _stream()), "fhe_ckks_encode")
+    return pt
+
+
+def fhe_ckks_decode(ctx: Context, pt, logQ: int, log_scale: float):
+    """pt: CUDA int32 tensor (cnum, ceil(logQ/32), N) of signed two's-complement limbs -> complex128 (cnum, N/2)."""
+    import torch
+
+    cnum = int(pt.shape[0])
+    z = torch.empty((cnum, ctx.N // 2), dtype=torch.complex128, device=ctx.device)
+    ws = ctx.workspace(FHE_OP_ENCODE, 1, cnum)
+    _check(lib.fhe_ckks_decode(ctx.handle, _dev(pt, torch.int32, (cnum, limbs(logQ), ctx.N)), cnum, int(logQ),
+                               float(log_scale), z.data_ptr(), ws.data_ptr(), ws.numel(), _stream()),
+           "fhe_ckks_decode")
+    return z
+
+
+def fhe_bgv_encode(ctx: Context, slots, logQ: int):
+    """slots: CUDA int32 tensor (cnum, N) of values mod t -> an encryption input (cnum, ceil(logQ/32), N)."""
+    import torch
+
+    cnum = int(slots.shape[0])
+    L = limbs(logQ)
+    pt = torch.zeros((cnum, L, ctx.N), dtype=torch.int32, device=ctx.device)
+    _check(lib.fhe_bgv_encode(ctx.handle, _dev(slots, torch.int32, (cnum, ctx.N)), cnum, pt.data_ptr(), L * ctx.N,
+                              _stream()), "fhe_bgv_encode")
+    return pt
+
+
+def fhe_bgv_decode(ctx: Context, coeffs):
+    """coeffs: CUDA int32 tensor (cnum, N) of plaintext coefficients mod t (fhe_decrypt's BGV output) -> slots."""
+    import torch
+
+    cnum = int(coeffs.shape[0])
+    slots = torch.empty((cnum, ctx.N), dtype=torch.int32, device=ctx.device)
+    _check(lib.fhe_bgv_decode(ctx.handle, _dev(coeffs, torch.int32, (cnum, ctx.N)), ctx.N, cnum, slots.data_ptr(),
+                              _stream()), "fhe_bgv_decode")
+    return slots
 
 
 def fhe_primes_for_bound(bound_bits: int) -> int:

@@ -4,8 +4,11 @@
 // Ring product (Sec. 5 pipeline): limb -> RNS lift -> forward NTT ->
 // pointwise -> INTT -> Garner -> limb, with the prime count sized to the
 // exact product's bound so the CRT result is the exact integer product.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <vector>
 
 #include "bgv.cuh"
 #include "common.cuh"
@@ -67,7 +70,8 @@ size_t words_rotate(const fhe_ctx* c, int logQ, int cnum) {
   const size_t N = c->N;
   const int rk = r_keyswitch(c, logQ), L = limbs_for_bits(logQ);
   if (rk < 0) return 0;
-  return (size_t)cnum * N * (2 * (size_t)L + 2 * (size_t)rk) + 2 * 64;
+  // transform of the centred a, the key products, kappa(b)
+  return (size_t)cnum * N * ((size_t)L + 3 * (size_t)rk) + 3 * 64;
 }
 size_t words_encrypt(const fhe_ctx* c, int cnum) {
   const int re = r_enc(c);
@@ -84,6 +88,13 @@ size_t words_ringmul(const fhe_ctx* c, int bits, int cnum) {
   if (r < 0) return 0;
   return (size_t)cnum * c->N * 2 * (size_t)r + 2 * 64;
 }
+
+// the seeded encryption's v (int8), e0, e1 (int32) ahead of the rest of the workspace
+size_t enc_sampler_bytes(const fhe_ctx* c, int cnum) {
+  const size_t n = (size_t)cnum * c->N;
+  return align256(n) + 2 * align256(4 * n);
+}
+size_t enc_sampler_words(const fhe_ctx* c, int cnum) { return enc_sampler_bytes(c, cnum) / 4; }
 
 bool is_bgv(const fhe_ctx* ctx) { return ctx->prm.scheme == FHE_SCHEME_BGV; }
 
@@ -139,28 +150,15 @@ int to_ntt_form(fhe_ctx* ctx, const uint32_t* src, int L, int npoly, int rows, u
   return check_launch();
 }
 
-uint32_t galois_of_step(int N, int step) {
-  // 5 has order N/2 modulo 2N
-  const long long ord = N / 2;
-  long long e = step % ord;
-  if (e < 0) e += ord;
-  uint64_t g = 1, b = 5, m = 2ull * N;
-  while (e) {
-    if (e & 1) g = g * b % m;
-    b = b * b % m;
-    e >>= 1;
-  }
-  return (uint32_t)g;
-}
-
 // Shared body of relinearisation and rotation key switching (Sec. 6):
 // Y = [nbatch][2][rk][N] whose block 0 holds the lifted c (limb poly to switch),
 // key K = [2][krows][N]; result (add + round(Y / P)) mod 2^logQ into out.
-int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int nbatch, int logQ, int k2,
-                    const uint32_t* add, size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out,
-                    cudaStream_t st, const int32_t* item_bits = nullptr, int out_limbs_pad = 0) {
+// The reconstruction of a key switch: (add + round(Y / P)) mod 2^(logQ - k2) from the coefficient-form
+// products Y = [nbatch][2][rk][N].
+int key_switch_epilogue(fhe_ctx* ctx, const uint32_t* Y, int rk, int nbatch, int logQ, int k2, const uint32_t* add,
+                        size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out, cudaStream_t st,
+                        const int32_t* item_bits = nullptr, int out_limbs_pad = 0) {
   const size_t N = ctx->N;
-  RET_IF(launch_ring_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
   EpiArgs epi;
   epi.kind = Epi::kRelin;
   epi.out_bits = logQ;
@@ -177,6 +175,78 @@ int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int n
   const size_t Lo = epi.out_limbs;
   RET_IF(launch_garner(ctx, Y, (size_t)rk * N, 2 * (size_t)rk * N, rk, 2, nbatch, out, Lo * N, 2 * Lo * N, epi, st));
   return check_launch();
+}
+
+int key_switch_tail(fhe_ctx* ctx, uint32_t* Y, const SwitchKey& K, int rk, int nbatch, int logQ, int k2,
+                    const uint32_t* add, size_t add_pstride, size_t add_bstride, int add_polys, uint32_t* out,
+                    cudaStream_t st, const int32_t* item_bits = nullptr, int out_limbs_pad = 0) {
+  RET_IF(launch_ring_key(ctx, Y, K.ntt, K.rows, rk, nbatch, st));
+  return key_switch_epilogue(ctx, Y, rk, nbatch, logQ, k2, add, add_pstride, add_bstride, add_polys, out, st,
+                             item_bits, out_limbs_pad);
+}
+
+// Automorphisms with key switching (Sec. 6 leftrotate_broadcast_into, conjugate_pairwise_into) of one
+// ciphertext batch for n Galois elements gs[s] -> outs[s]:
+//   outs[s] = (kappa(b), 0) + round(P^-1 kappa(centred a) rtk mod P Q)  (mod Q),
+// kappa taken over Z on the centred representative of a (two's complement of logQ bits).  The
+// centred a is lifted and transformed once; each kappa is then a row gather in the transform
+// domain in front of the key products (hoisting), so n rotations cost one lift and one forward
+// transform in all, plus per step the key products, two inverse transforms and the reconstruction.
+int rotate_many(fhe_ctx* ctx, const fhe_ct* in, const uint32_t* gs, int n, fhe_ct* const* outs, void* ws,
+                size_t ws_bytes, cudaStream_t st) {
+  const int cnum = in->cnum, logQ = in->logQ, L = limbs_for_bits(logQ), rk = r_keyswitch(ctx, logQ);
+  const size_t N = ctx->N;
+  std::vector<const SwitchKey*> keys(n);
+  for (int s = 0; s < n; ++s) {
+    auto it = ctx->rtk.find(gs[s]);
+    if (it == ctx->rtk.end()) {
+      set_error("rotate: no switching key for the Galois element %u", gs[s]);
+      return FHE_ENOKEY;
+    }
+    keys[s] = &it->second;
+  }
+  Carve cv(ws, ws_bytes);
+  uint32_t* AH = cv.take((size_t)cnum * rk * N);
+  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
+  uint32_t* KB = cv.take((size_t)cnum * L * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("rotate: workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  RET_IF(launch_lift_signed(ctx, in->data + (size_t)L * N, L, 0, 2 * (size_t)L * N, AH, 0, (size_t)rk * N, 1, cnum,
+                            rk, logQ, nullptr, st));
+  RET_IF(launch_ntt(ctx, AH, cnum, rk, rk, rk, false, st));
+  for (int s = 0; s < n; ++s) {
+    RET_IF(launch_automorph(ctx, in->data, 2 * (size_t)L * N, KB, (size_t)L * N, L, logQ, gs[s], cnum, st));
+    RET_IF(launch_key_perm(ctx, AH, Y, keys[s]->ntt, keys[s]->rows, rk, cnum, gs[s], st));
+    RET_IF(key_switch_epilogue(ctx, Y, rk, cnum, logQ, 0, KB, 0, (size_t)L * N, 1, outs[s]->data, st));
+    outs[s]->log_scale = in->log_scale;
+  }
+  return FHE_OK;
+}
+
+int rotate_checks(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* const* outs, int n, const char* who) {
+  if (ctx && is_bgv(ctx)) {
+    set_error("%s: CKKS only", who);
+    return FHE_EINVAL;
+  }
+  if (!ctx || !ct_ok(ctx, in) || n < 1 || !outs) {
+    set_error("%s: bad arguments", who);
+    return FHE_EINVAL;
+  }
+  for (int s = 0; s < n; ++s) {
+    const fhe_ct* o = outs[s];
+    if (!ct_ok(ctx, o) || o->logQ != in->logQ || o->cnum != in->cnum || o->data == in->data) {
+      set_error("%s: output %d malformed, of another level or batch size, or aliasing the input", who, s);
+      return FHE_EINVAL;
+    }
+    for (int t = 0; t < s; ++t)
+      if (outs[t]->data == o->data) {
+        set_error("%s: outputs %d and %d alias", who, t, s);
+        return FHE_EINVAL;
+      }
+  }
+  return FHE_OK;
 }
 
 // BGV multiplication at level l: exact tensor product reduced mod Q_l, then the
@@ -202,7 +272,7 @@ int mult_bgv(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* 
   }
   const size_t ctw = 2 * (size_t)L * N;
   RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
-  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
+  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, b->cnum == 1 ? 0 : ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
                      4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_ring_tensor(ctx, X, rt, cnum, st));
   EpiArgs e0;
@@ -255,8 +325,8 @@ int mult_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* ou
   e0.out_limbs = L;
   RET_IF(launch_garner(ctx, X, (size_t)rt * N, 4 * (size_t)rt * N, rt, 3, cnum, D, (size_t)L * N,
                        3 * (size_t)L * N, e0, st));
-  RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
-                     st));
+  RET_IF(launch_lift_signed(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum,
+                            rk, 0, item_bits, st));
   return key_switch_tail(ctx, Y, ctx->evk, rk, cnum, logQ_max, k2, D, (size_t)L * N, 3 * (size_t)L * N, 2, out, st,
                          item_bits, L);
 }
@@ -267,8 +337,8 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
     set_error("mult: null or malformed argument");
     return FHE_EINVAL;
   }
-  if (a->logQ != b->logQ || a->cnum != b->cnum || out->cnum != a->cnum) {
-    set_error("mult: operands differ in level or batch size");
+  if (a->logQ != b->logQ || (a->cnum != b->cnum && b->cnum != 1) || out->cnum != a->cnum) {
+    set_error("mult: operands differ in level or batch size (b->cnum must equal a->cnum, or be 1 to broadcast)");
     return FHE_ELEVEL;
   }
   if (k2 < 0 || out->logQ != a->logQ - k2 || out->logQ < 1) {
@@ -304,8 +374,9 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ctw = 2 * (size_t)L * N;  // words per input ciphertext
   // tensor product: lift (b1, a1) and (b2, a2), 4 forward NTTs, Karatsuba, 3 INTTs, Garner
+  const size_t btw = b->cnum == 1 ? 0 : ctw;  // broadcast mode: every item reads the one b
   RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
-  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, ctw, X + 2 * (size_t)rt * N, (size_t)rt * N,
+  RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, btw, X + 2 * (size_t)rt * N, (size_t)rt * N,
                      4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_ring_tensor(ctx, X, rt, cnum, st));
   EpiArgs e0;
@@ -314,11 +385,13 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
   e0.out_limbs = L;
   RET_IF(launch_garner(ctx, X, (size_t)rt * N, 4 * (size_t)rt * N, rt, 3, cnum, D, (size_t)L * N,
                        3 * (size_t)L * N, e0, st));
-  // relinearisation: d2 -> rk primes, times evk, round(/P), + (d0, d1), optional rescale
-  RET_IF(launch_lift(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk,
-                     st));
-  return key_switch_tail(ctx, Y, ctx->evk, rk, cnum, logQ, k2, D, (size_t)L * N, 3 * (size_t)L * N, 2, out->data,
-                         st);
+  // relinearisation: centred d2 -> rk primes, times evk, round(/P), + (d0, d1), optional rescale
+  RET_IF(launch_lift_signed(ctx, D + 2 * (size_t)L * N, L, 0, 3 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum,
+                            rk, logQ, nullptr, st));
+  RET_IF(key_switch_tail(ctx, Y, ctx->evk, rk, cnum, logQ, k2, D, (size_t)L * N, 3 * (size_t)L * N, 2, out->data,
+                         st));
+  out->log_scale = a->log_scale + b->log_scale - k2;
+  return FHE_OK;
 }
 
 }  // namespace
@@ -386,6 +459,16 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
       return FHE_EINVAL;
     }
   }
+  if (p->hamming_weight < 0 || p->hamming_weight > (1 << p->logN) || p->sigma < 0.0 || p->sigma > kMaxGaussSigma) {
+    set_error("ctx_create: hamming_weight %d (0..N) or sigma %g (0..%g) out of range", p->hamming_weight, p->sigma,
+              kMaxGaussSigma);
+    return FHE_EINVAL;
+  }
+  GaussTable gt;
+  if (gauss_table(p->sigma > 0.0 ? p->sigma : kDefaultSigma, &gt) != FHE_OK) {
+    set_error("ctx_create: sigma %g gives no usable rounded-Gaussian table", p->sigma);
+    return FHE_EINVAL;
+  }
   const int R = primes_for_bound_global(p->logN + 2 * p->logQ + p->logP);
   if (R < 0) {
     set_error("ctx_create: more than %d primes needed", kMaxPrimes);
@@ -399,6 +482,7 @@ int fhe_ctx_create(const fhe_params* p, fhe_alloc_fn alloc, fhe_free_fn free_, v
   ctx->alloc_user = user;
   ctx->R = R;
   ctx->crt_mode = p->crt;
+  ctx->gauss = gt;
   cudaGetDevice(&ctx->device);
   int rc = build_tables(ctx);
   if (rc == FHE_OK && p->scheme == FHE_SCHEME_BGV) {
@@ -450,6 +534,7 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
       break;
     case FHE_OP_ENCRYPT:
       w = words_encrypt(ctx, cnum);
+      if (w) w += enc_sampler_words(ctx, cnum);
       if (w && is_bgv(ctx))
         w += (size_t)cnum * ctx->N * 2 * bgv_prod_limbs(ctx->prm.logN + ctx->prm.logQ) + 64;
       break;
@@ -466,6 +551,17 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
     case FHE_OP_RING_MUL:
       w = words_ringmul(ctx, logQ, cnum);
       break;
+    case FHE_OP_MULT_PLAIN:
+      if (logQ > ctx->prm.logQ || is_bgv(ctx)) return 0;
+      {
+        const int r = r_tensor(ctx, logQ);
+        if (r < 0) return 0;
+        w = (size_t)cnum * ctx->N * 3 * (size_t)r + 2 * 64;  // the batch's two polynomials and up to cnum plaintexts
+      }
+      break;
+    case FHE_OP_ENCODE:
+      w = (size_t)cnum * ctx->N * 8;  // two complex double buffers
+      break;
     case FHE_OP_MULT_RAGGED:
       if (logQ > ctx->prm.logQ) return 0;
       w = words_mult(ctx, logQ, cnum);
@@ -476,8 +572,8 @@ size_t fhe_workspace_bytes(const fhe_ctx* ctx, int op, int logQ, int cnum) {
   return w ? w * 4 + 1024 : 0;
 }
 
-int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk, const uint32_t* a_ev,
-               const int32_t* e_ev) {
+int fhe_keygen_inject(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_t* e_pk,
+                      const uint32_t* a_ev, const int32_t* e_ev) {
   if (!ctx || !s || !a_pk || !e_pk || !a_ev || !e_ev) {
     set_error("keygen: null argument");
     return FHE_EINVAL;
@@ -634,37 +730,42 @@ int fhe_keygen(fhe_ctx* ctx, const int8_t* s, const uint32_t* a_pk, const int32_
   return FHE_OK;
 }
 
-int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e) {
+}  // extern "C"
+
+namespace {
+
+// Switching key of the automorphism X -> X^g (rotation or conjugation, Sec. 6 rtk / ck):
+// (-a s + e + P s(X^g), a) mod P Q in NTT form, stored under g.
+int keygen_switch(fhe_ctx* ctx, uint32_t g, const uint32_t* a, const int32_t* e, const char* who) {
   if (ctx && is_bgv(ctx)) {
-    set_error("keygen_rotation: CKKS only");
+    set_error("%s: CKKS only", who);
     return FHE_EINVAL;
   }
   if (!ctx || !a || !e) {
-    set_error("keygen_rotation: null argument");
+    set_error("%s: null argument", who);
     return FHE_EINVAL;
   }
   if (!ctx->have_keys) {
-    set_error("keygen_rotation: call fhe_keygen first");
+    set_error("%s: generate the key set first", who);
     return FHE_ENOKEY;
   }
   const size_t N = ctx->N;
   const int logQ = ctx->prm.logQ, logP = ctx->prm.logP;
   const int Lpq = limbs_for_bits(logQ + logP), R = ctx->R;
-  const uint32_t g = galois_of_step(ctx->N, step);
   SwitchKey& K = ctx->rtk[g];
   if (!K.ntt) {
     K.ntt = (uint32_t*)ctx_alloc(ctx, 2 * (size_t)R * N * 4);
     K.rows = R;
     if (!K.ntt) {
       ctx->rtk.erase(g);
-      set_error("keygen_rotation: allocation failed");
+      set_error("%s: allocation failed", who);
       return FHE_ENOMEM;
     }
   }
   const size_t scratch_words = (size_t)N * (1 + 1 + Lpq + Lpq + 2 * Lpq) + 2 * (size_t)R * N;
   uint32_t* scratch = (uint32_t*)ctx_alloc(ctx, scratch_words * 4);
   if (!scratch) {
-    set_error("keygen_rotation: scratch allocation failed");
+    set_error("%s: scratch allocation failed", who);
     return FHE_ENOMEM;
   }
   auto fail = [&](int code) {
@@ -680,7 +781,7 @@ int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t
   cudaStream_t st = 0;
   if (cudaMemcpy(d_e, e, N * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(d_a, a, (size_t)Lpq * N * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-    set_error("keygen_rotation: upload failed");
+    set_error("%s: upload failed", who);
     return fail(FHE_ECUDA);
   }
   int rc = launch_automorph_small(ctx, ctx->d_s, d_ks, g, st);
@@ -698,15 +799,67 @@ int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t
     return fail(FHE_ECUDA);
   if ((rc = to_ntt_form(ctx, d_kl, Lpq, 2, R, K.ntt, st))) return fail(rc);
   if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-    set_error("keygen_rotation: device error");
+    set_error("%s: device error", who);
     return fail(FHE_ECUDA);
   }
   ctx_free(ctx, scratch);
   return FHE_OK;
 }
 
-int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1, fhe_ct* out,
-                void* ws, size_t ws_bytes, void* stream) {
+}  // namespace
+
+extern "C" {
+
+int fhe_keygen_rotation(fhe_ctx* ctx, int step, const uint32_t* a, const int32_t* e) {
+  return keygen_switch(ctx, ctx ? galois_of_step(ctx->N, step) : 0u, a, e, "keygen_rotation");
+}
+
+int fhe_keygen_conjugation(fhe_ctx* ctx, const uint32_t* a, const int32_t* e) {
+  return keygen_switch(ctx, ctx ? 2u * ctx->N - 1u : 0u, a, e, "keygen_conjugation");
+}
+
+int fhe_keygen(fhe_ctx* ctx, uint64_t seed, const int* rot_steps, int n_rot) {
+  if (!ctx || n_rot < 0 || (n_rot > 0 && !rot_steps)) {
+    set_error("keygen: null context or bad rotation-step list");
+    return FHE_EINVAL;
+  }
+  const int N = ctx->N, logQ = ctx->prm.logQ, logP = ctx->prm.logP;
+  const bool bgv = is_bgv(ctx);
+  // BGV reduces the uniform parts modulo Q and P Q itself: draw whole limbs
+  const int bq = bgv ? 32 * limbs_for_bits(logQ) : logQ;
+  const int bpq = bgv ? 32 * limbs_for_bits(logQ + logP) : logQ + logP;
+  std::vector<int8_t> s(N);
+  if (ctx->prm.hamming_weight > 0)
+    sample_sparse_ternary(seed, kTagSecret, 0, N, ctx->prm.hamming_weight, s.data());
+  else
+    sample_ternary(seed, kTagSecret, 0, N, s.data());
+  std::vector<uint32_t> a_pk((size_t)limbs_for_bits(bq) * N), a_ev((size_t)limbs_for_bits(bpq) * N);
+  std::vector<int32_t> e_pk(N), e_ev(N);
+  sample_uniform_limbs(seed, kTagPkA, 0, N, bq, a_pk.data());
+  sample_gaussian(seed, kTagPkE, 0, N, ctx->gauss, e_pk.data());
+  sample_uniform_limbs(seed, kTagEvA, 0, N, bpq, a_ev.data());
+  sample_gaussian(seed, kTagEvE, 0, N, ctx->gauss, e_ev.data());
+  RET_IF(fhe_keygen_inject(ctx, s.data(), a_pk.data(), e_pk.data(), a_ev.data(), e_ev.data()));
+  if (bgv) {
+    if (n_rot > 0) {
+      set_error("keygen: rotation keys are CKKS only");
+      return FHE_EINVAL;
+    }
+    return FHE_OK;
+  }
+  std::vector<uint32_t> a((size_t)limbs_for_bits(logQ + logP) * N);
+  std::vector<int32_t> e(N);
+  auto one = [&](uint32_t g, const char* who) {
+    sample_uniform_limbs(seed, kTagSwA, g, N, logQ + logP, a.data());
+    sample_gaussian(seed, kTagSwE, g, N, ctx->gauss, e.data());
+    return keygen_switch(ctx, g, a.data(), e.data(), who);
+  };
+  for (int i = 0; i < n_rot; ++i) RET_IF(one(galois_of_step(N, rot_steps[i]), "keygen (rotation key)"));
+  return one(2u * N - 1u, "keygen (conjugation key)");
+}
+
+int fhe_encrypt_inject(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t* e0, const int32_t* e1,
+                       fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
   if (!ctx || !pt || !v || !e0 || !e1 || !ct_ok(ctx, out)) {
     set_error("encrypt: null or malformed argument");
     return FHE_EINVAL;
@@ -758,6 +911,30 @@ int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, const int8_t* v, const int32_t
   RET_IF(launch_garner(ctx, Y, (size_t)re * N, 2 * (size_t)re * N, re, 2, cnum, out->data, (size_t)L * N,
                        2 * (size_t)L * N, e, st));
   return check_launch();
+}
+
+int fhe_encrypt(fhe_ctx* ctx, const uint32_t* pt, uint64_t seed, fhe_ct* out, void* ws, size_t ws_bytes,
+                void* stream) {
+  if (!ctx || !pt || !ct_ok(ctx, out)) {
+    set_error("encrypt: null or malformed argument");
+    return FHE_EINVAL;
+  }
+  const size_t head = enc_sampler_bytes(ctx, out->cnum);
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < head) {
+    set_error("encrypt: workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  const size_t n = (size_t)out->cnum * ctx->N;
+  int8_t* v = (int8_t*)ws;
+  int32_t* e0 = (int32_t*)((uint8_t*)ws + align256(n));
+  int32_t* e1 = (int32_t*)((uint8_t*)ws + align256(n) + align256(4 * n));
+  if (!ctx->have_keys) {
+    set_error("encrypt: no public key");
+    return FHE_ENOKEY;
+  }
+  RET_IF(launch_sample_enc(ctx, seed, out->cnum, v, e0, e1, (cudaStream_t)stream));
+  RET_IF(check_launch());
+  return fhe_encrypt_inject(ctx, pt, v, e0, e1, out, (uint8_t*)ws + head, ws_bytes - head, stream);
 }
 
 int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size_t ws_bytes, void* stream) {
@@ -857,6 +1034,7 @@ int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream
     return FHE_EINVAL;
   }
   RET_IF(launch_rescale(ctx, in->data, in->logQ, out->data, k, in->cnum * 2, (cudaStream_t)stream));
+  out->log_scale = in->log_scale - k;
   return check_launch();
 }
 
@@ -880,6 +1058,7 @@ int fhe_moddown(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
     return FHE_EINVAL;
   }
   RET_IF(launch_moddown(ctx, in->data, in->logQ, out->data, out->logQ, in->cnum * 2, (cudaStream_t)stream));
+  out->log_scale = in->log_scale;
   return check_launch();
 }
 
@@ -888,9 +1067,15 @@ static int addsub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, i
     set_error("add/sub/negate: bad arguments");
     return FHE_EINVAL;
   }
-  if ((mode != 2 && (b->logQ != a->logQ || b->cnum != a->cnum)) || out->logQ != a->logQ || out->cnum != a->cnum) {
-    set_error("add/sub/negate: operand levels differ");
+  const bool bcast = mode != 2 && b->cnum == 1 && a->cnum > 1;
+  if ((mode != 2 && (b->logQ != a->logQ || (b->cnum != a->cnum && !bcast))) || out->logQ != a->logQ ||
+      out->cnum != a->cnum) {
+    set_error("add/sub/negate: operand levels or batch sizes differ (b->cnum must equal a->cnum, or be 1)");
     return FHE_ELEVEL;
+  }
+  if (bcast && (out->data == b->data || is_bgv(ctx))) {
+    set_error("add/sub (broadcast): CKKS only, out must not alias the broadcast operand");
+    return FHE_EINVAL;
   }
   if (is_bgv(ctx)) {
     if ((mode != 2 && b->level != a->level) || out->level != a->level) {
@@ -901,8 +1086,13 @@ static int addsub(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, i
                              (cudaStream_t)stream));
     return check_launch();
   }
+  if (mode != 2 && fabs(a->log_scale - b->log_scale) > 1e-9) {
+    set_error("add/sub: operand scales differ (2^%g vs 2^%g)", a->log_scale, b->log_scale);
+    return FHE_ELEVEL;
+  }
   RET_IF(launch_addsub(ctx, a->data, mode == 2 ? a->data : b->data, out->data, a->logQ, a->cnum * 2, mode,
-                       (cudaStream_t)stream));
+                       (cudaStream_t)stream, bcast ? 2 : 0));
+  out->log_scale = a->log_scale;
   return check_launch();
 }
 int fhe_add(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, fhe_ct* out, void* stream) {
@@ -925,6 +1115,7 @@ int fhe_mult_const(fhe_ctx* ctx, const fhe_ct* in, int32_t c, fhe_ct* out, void*
     return FHE_EINVAL;
   }
   RET_IF(launch_mult_const(ctx, in->data, c, out->data, in->logQ, in->cnum * 2, (cudaStream_t)stream));
+  out->log_scale = in->log_scale;
   return check_launch();
 }
 
@@ -937,39 +1128,96 @@ int fhe_add_const(fhe_ctx* ctx, const fhe_ct* in, int64_t value, int shift, fhe_
   const size_t bytes = fhe_ct_bytes(ctx->prm.logN, in->logQ, in->cnum);
   if (out->data != in->data)
     FHE_CHECK_CUDA(cudaMemcpyAsync(out->data, in->data, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-  RET_IF(launch_add_const(ctx, out->data, out->data, value, shift, in->logQ, in->cnum, (cudaStream_t)stream));
+  RET_IF(launch_add_const(ctx, out->data, out->data, value, nullptr, shift, in->logQ, in->cnum,
+                          (cudaStream_t)stream));
+  out->log_scale = in->log_scale;
+  return check_launch();
+}
+
+int fhe_add_const_vec(fhe_ctx* ctx, const fhe_ct* in, const int64_t* values, int shift, fhe_ct* out, void* stream) {
+  if (!ctx || !values || is_bgv(ctx) || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ ||
+      out->cnum != in->cnum || shift < 0 || shift >= in->logQ) {
+    set_error("add_const_vec: bad arguments (CKKS, values non-null, 0 <= shift < logQ)");
+    return FHE_EINVAL;
+  }
+  const size_t bytes = fhe_ct_bytes(ctx->prm.logN, in->logQ, in->cnum);
+  if (out->data != in->data)
+    FHE_CHECK_CUDA(cudaMemcpyAsync(out->data, in->data, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  RET_IF(launch_add_const(ctx, out->data, out->data, 0, values, shift, in->logQ, in->cnum, (cudaStream_t)stream));
+  out->log_scale = in->log_scale;
+  return check_launch();
+}
+
+int fhe_imult(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* stream) {
+  if (!ctx || is_bgv(ctx) || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
+      out->data == in->data) {
+    set_error("imult: bad arguments (CKKS, same level and batch, no aliasing)");
+    return FHE_EINVAL;
+  }
+  RET_IF(launch_monomial(ctx, in->data, out->data, in->logQ, ctx->N / 2, in->cnum * 2, (cudaStream_t)stream));
+  out->log_scale = in->log_scale;
+  return check_launch();
+}
+
+int fhe_mult_plain(fhe_ctx* ctx, const fhe_ct* in, const uint32_t* pt, int pt_cnum, double pt_log_scale, fhe_ct* out,
+                   void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || is_bgv(ctx) || !pt || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ ||
+      out->cnum != in->cnum || out->data == in->data || (pt_cnum != 1 && pt_cnum != in->cnum)) {
+    set_error("mult_plain: bad arguments (CKKS, pt_cnum 1 or cnum, same level and batch, no aliasing)");
+    return FHE_EINVAL;
+  }
+  const int cnum = in->cnum, logQ = in->logQ, L = limbs_for_bits(logQ), r = r_tensor(ctx, logQ);
+  const size_t N = ctx->N;
+  Carve cv(ws, ws_bytes);
+  uint32_t* X = cv.take((size_t)cnum * 2 * r * N);
+  uint32_t* M = cv.take((size_t)pt_cnum * r * N);
+  if (!cv.ok || ((uintptr_t)ws & 255)) {
+    set_error("mult_plain: workspace of %zu bytes too small or misaligned", ws_bytes);
+    return FHE_EWORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t rN = (size_t)r * N;
+  RET_IF(launch_lift(ctx, in->data, L, (size_t)L * N, 2 * (size_t)L * N, X, rN, 2 * rN, 2, cnum, r, st));
+  RET_IF(launch_lift(ctx, pt, L, 0, (size_t)L * N, M, 0, rN, 1, pt_cnum, r, st));
+  RET_IF(launch_ntt(ctx, X, cnum * 2, r, r, r, false, st));
+  RET_IF(launch_ntt(ctx, M, pt_cnum, r, r, r, false, st));
+  for (int p = 0; p < 2; ++p)
+    RET_IF(launch_pointwise_mul_strided(ctx, X + p * rN, 2 * rN, X + p * rN, 2 * rN, M, pt_cnum == 1 ? 0 : rN, r, cnum,
+                                        st));
+  RET_IF(launch_ntt(ctx, X, cnum * 2, r, r, r, true, st));
+  EpiArgs e;
+  e.kind = Epi::kStore;
+  e.out_bits = logQ;
+  e.out_limbs = L;
+  RET_IF(launch_garner(ctx, X, rN, 2 * rN, r, 2, cnum, out->data, (size_t)L * N, 2 * (size_t)L * N, e, st));
+  out->log_scale = in->log_scale + pt_log_scale;
   return check_launch();
 }
 
 int fhe_rotate(fhe_ctx* ctx, const fhe_ct* in, int step, fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
-  if (ctx && is_bgv(ctx)) {
-    set_error("rotate: CKKS only");
-    return FHE_EINVAL;
-  }
-  if (!ctx || !ct_ok(ctx, in) || !ct_ok(ctx, out) || out->logQ != in->logQ || out->cnum != in->cnum ||
-      out->data == in->data) {
-    set_error("rotate: bad arguments");
-    return FHE_EINVAL;
-  }
+  fhe_ct* outs[1] = {out};
+  RET_IF(rotate_checks(ctx, in, outs, 1, "rotate"));
   const uint32_t g = galois_of_step(ctx->N, step);
-  auto it = ctx->rtk.find(g);
-  if (it == ctx->rtk.end()) {
-    set_error("rotate: no rotation key for step %d (g = %u)", step, g);
-    return FHE_ENOKEY;
+  return rotate_many(ctx, in, &g, 1, outs, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int fhe_rotate_hoisted(fhe_ctx* ctx, const fhe_ct* in, const int* steps, int nsteps, fhe_ct* const* outs, void* ws,
+                       size_t ws_bytes, void* stream) {
+  if (!steps || nsteps < 1 || nsteps > 4096) {
+    set_error("rotate_hoisted: steps null or nsteps %d out of 1..4096", nsteps);
+    return FHE_EINVAL;
   }
-  const int cnum = in->cnum, logQ = in->logQ, L = limbs_for_bits(logQ), rk = r_keyswitch(ctx, logQ);
-  const size_t N = ctx->N;
-  Carve cv(ws, ws_bytes);
-  uint32_t* KB = cv.take((size_t)cnum * 2 * L * N);
-  uint32_t* Y = cv.take((size_t)cnum * 2 * rk * N);
-  if (!cv.ok || ((uintptr_t)ws & 255)) {
-    set_error("rotate: workspace too small or misaligned");
-    return FHE_EWORKSPACE;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  RET_IF(launch_automorph(ctx, in->data, (size_t)L * N, KB, (size_t)L * N, L, logQ, g, cnum * 2, st));
-  RET_IF(launch_lift(ctx, KB + (size_t)L * N, L, 0, 2 * (size_t)L * N, Y, 0, 2 * (size_t)rk * N, 1, cnum, rk, st));
-  return key_switch_tail(ctx, Y, it->second, rk, cnum, logQ, 0, KB, 0, 2 * (size_t)L * N, 1, out->data, st);
+  RET_IF(rotate_checks(ctx, in, outs, nsteps, "rotate_hoisted"));
+  std::vector<uint32_t> gs(nsteps);
+  for (int s = 0; s < nsteps; ++s) gs[s] = galois_of_step(ctx->N, steps[s]);
+  return rotate_many(ctx, in, gs.data(), nsteps, outs, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int fhe_conjugate(fhe_ctx* ctx, const fhe_ct* in, fhe_ct* out, void* ws, size_t ws_bytes, void* stream) {
+  fhe_ct* outs[1] = {out};
+  RET_IF(rotate_checks(ctx, in, outs, 1, "conjugate"));
+  const uint32_t g = 2u * ctx->N - 1u;
+  return rotate_many(ctx, in, &g, 1, outs, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int Lb, int logOut, uint32_t* out,

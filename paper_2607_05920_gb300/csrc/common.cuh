@@ -21,6 +21,18 @@ constexpr int kMaxLiftLimbs = 128; // widest operand a ring product lifts
 constexpr int kLiftDigits = 64;    // 24-bit digits of the digit-lift path (operands up to 48 limbs)
 constexpr int kCrtDigits = 176;    // 24-bit digit columns of the direct CRT (22 blocks of 8)
 constexpr int kMaxLogN = 16;
+constexpr int kMaxGaussB = 60;          // widest rounded-Gaussian support |e| <= B, B = floor(6 sigma)
+constexpr double kMaxGaussSigma = 10.0;
+constexpr double kDefaultSigma = 3.2;
+// sampler stream tags (tag0) of the seeded key generation and encryption
+constexpr uint32_t kTagSecret = 1, kTagPkA = 2, kTagPkE = 3, kTagEvA = 4, kTagEvE = 5, kTagSwA = 6, kTagSwE = 7,
+                   kTagEncV = 8;
+
+// Thresholds of the rounded-Gaussian sampler (see sampler.cu).
+struct GaussTable {
+  uint32_t thr[2 * kMaxGaussB];
+  int B = 0;
+};
 
 // Error reporting (thread-local message, see fhe_last_error).
 void set_error(const char* fmt, ...);
@@ -112,6 +124,7 @@ struct fhe_ctx {
   // and per L the folded offset + 2^17 q_i, [kMaxLiftLimbs + 1][R] (see k_lift_tc)
   uint16_t* d_lift_tc = nullptr;
   uint64_t* d_lift_off = nullptr;
+  uint64_t* d_lift_off_s = nullptr;  // the same offsets for the signed (two's-complement) lift
   std::vector<size_t> crt_tc_off;
   std::vector<uint8_t> crt_tc_exact22;  // per r: every column sum is below 2^22 in magnitude
   int crt_tc_mt = 0;              // output byte columns covered, in 16s
@@ -122,6 +135,10 @@ struct fhe_ctx {
   fhe::BgvLevel* d_bgv_levels = nullptr;
   fhe::BgvConsts* d_bgv_consts = nullptr;
   std::vector<int> bgv_bits;
+  uint32_t* d_bgv_slots = nullptr;  // slot batching tables mod t (built on first use, see k_encode.cu)
+
+  // rounded-Gaussian sampler table for params.sigma (seeded encryption and key generation)
+  fhe::GaussTable gauss;
 
   // keys (resident)
   bool have_keys = false;
@@ -154,6 +171,33 @@ void free_all(fhe_ctx* ctx);
 const char* last_error();
 
 inline int limbs_for_bits(int bits) { return (bits + 31) / 32; }
+
+// Galois element 5^step mod 2N of a left rotation by `step` slots (5 has order N/2 mod 2N;
+// negative steps rotate right).
+inline uint32_t galois_of_step(int N, int step) {
+  const long long ord = N / 2;
+  long long e = step % ord;
+  if (e < 0) e += ord;
+  uint64_t g = 1, b = 5, m = 2ull * N;
+  while (e) {
+    if (e & 1) g = g * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return (uint32_t)g;
+}
+
+// --------------------------------------------------------------- sampler
+// Counter-based sampler (Philox4x32-10) of sampler.cu: host draws for key generation, a kernel
+// for the randomness of seeded encryption.
+int gauss_table(double sigma, GaussTable* gt);
+void sample_uniform_limbs(uint64_t seed, uint32_t tag0, uint32_t tag1, int n, int bits, uint32_t* out);
+void sample_ternary(uint64_t seed, uint32_t tag0, uint32_t tag1, int n, int8_t* out);
+void sample_sparse_ternary(uint64_t seed, uint32_t tag0, uint32_t tag1, int n, int h, int8_t* out);
+void sample_gaussian(uint64_t seed, uint32_t tag0, uint32_t tag1, int n, const GaussTable& gt, int32_t* out);
+// v: int8 [cnum][N], e0 / e1: int32 [cnum][N] (device)
+int launch_sample_enc(const fhe_ctx* ctx, uint64_t seed, int cnum, int8_t* v, int32_t* e0, int32_t* e1,
+                      cudaStream_t st);
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------ device arithmetic
@@ -198,6 +242,13 @@ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) 
 int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
                 uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r,
                 cudaStream_t st);
+// The same lift of signed values: batch item b holds the two's-complement integer of
+// bits(b) = item_bits ? item_bits[b] : sbits bits (bit bits(b) - 1 is the sign, limbs at and above
+// bit bits(b) are ignored), i.e. the centred representative in [-2^(bits-1), 2^(bits-1)) of a value
+// mod 2^bits.  L < kMaxLiftLimbs.
+int launch_lift_signed(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
+                       uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r, int sbits,
+                       const int32_t* item_bits, cudaStream_t st);
 // Lift of small signed int32 (or int8 when is_i8) coefficients.
 int launch_lift_small(const fhe_ctx* ctx, const void* src, bool is_i8, size_t src_bstride, uint32_t* dst,
                       size_t dst_bstride, int nbatch, int r, cudaStream_t st);
@@ -220,10 +271,20 @@ int launch_pointwise_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, 
 int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st);
 int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
                     cudaStream_t st);
+// Key switch of an automorphism kappa_g (rotation, conjugation) from the forward transform of its
+// input: AH = [nbatch][r][N] (transform form, fully reduced), K = [2][krows][N]; writes
+// Y = [nbatch][2][r][N] = the coefficient-form products kappa_g(a) K_b, kappa_g(a) K_a (one
+// Montgomery factor removed by the inverse transform's scale, as in launch_ring_key).
+int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const uint32_t* K, int krows, int r,
+                    int nbatch, uint32_t g, cudaStream_t st);
 //  key: Y = [nbatch][2][r][N]; row block 0 holds D (in), outputs D*K_b into block 0 and
 //  D*K_a into block 1 with K = [2][krows][N] (first r rows used).
 int launch_pointwise_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,
                          cudaStream_t st);
+//  Z at batch stride z_bstride (the plain form: r N)
+int launch_pointwise_mul_strided(const fhe_ctx* ctx, uint32_t* Z, size_t z_bstride, const uint32_t* A,
+                                 size_t a_bstride, const uint32_t* B, size_t b_bstride, int r, int nbatch,
+                                 cudaStream_t st);
 //  general: Z[b][k][n] = A[b][k][n] * B[(b*bstride_b)][k][n]  (bstride_b 0 = broadcast)
 int launch_pointwise_mul(const fhe_ctx* ctx, uint32_t* Z, const uint32_t* A, size_t a_bstride, const uint32_t* B,
                          size_t b_bstride, int r, int nbatch, cudaStream_t st);
@@ -266,12 +327,16 @@ int launch_rescale(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t
                    cudaStream_t st);
 int launch_moddown(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t* out, int logQ_out, int npolys,
                    cudaStream_t st);
+// b_polys > 0: b is that many polynomials reused for every group of b_polys outputs (broadcast)
 int launch_addsub(const fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int logQ, int npolys,
-                  int mode /*0 add,1 sub,2 neg(a)*/, cudaStream_t st);
+                  int mode /*0 add,1 sub,2 neg(a)*/, cudaStream_t st, int b_polys = 0);
+// out = in X^k (0 <= k < N), polys of ceil(logQ/32) limbs mod 2^logQ; out must not alias in.
+int launch_monomial(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int logQ, int k, int npolys,
+                    cudaStream_t st);
 int launch_mult_const(const fhe_ctx* ctx, const uint32_t* in, int32_t c, uint32_t* out, int logQ, int npolys,
                       cudaStream_t st);
-int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, int shift, int logQ,
-                     int cnum, cudaStream_t st);
+int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, const int64_t* values,
+                     int shift, int logQ, int cnum, cudaStream_t st);
 // out[l][n] = sign * in[l][i], kappa_g (X^i -> X^(i g)); polys of L limbs mod 2^logQ.
 int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, uint32_t* out, size_t out_pstride,
                      int L, int logQ, uint32_t g, int npolys, cudaStream_t st);

@@ -1192,6 +1192,26 @@ static int tc_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size_t i
   return 1;
 }
 
+// Self-test of the timeout path: one thread waits on a shared-memory mbarrier that nothing
+// arrives on, with at most `tries` polls of a short suspend hint; when they run out it records the
+// timeout in the status word (as every pipeline wait of the tensor-core kernels does) and returns.
+__global__ void k_wait_selftest(int tries) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_addr(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  for (int it = 0; it < tries; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(0u), "r"(1000u)
+        : "memory");
+    if (ok) return;  // cannot happen: no thread arrives
+  }
+  atomicOr(&FHE_TC_STATUS, 1u);
+}
+
 // Device status word: nonzero after a bounded wait gave up.  Read and cleared.
 unsigned int read_dev_status() {
   unsigned int v = 0, z = 0;
@@ -1277,3 +1297,13 @@ int launch_garner(const fhe_ctx* ctx, const uint32_t* in, size_t in_pstride, siz
 }
 
 }  // namespace fhe
+
+extern "C" int fhe_selftest_wait_timeout(int tries, void* stream) {
+  if (tries < 1 || tries > 100000) {
+    fhe::set_error("selftest_wait_timeout: tries %d out of 1..100000", tries);
+    return FHE_EINVAL;
+  }
+  fhe::k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(tries);
+  FHE_CHECK_CUDA(cudaGetLastError());
+  return FHE_OK;
+}

@@ -22,6 +22,25 @@ namespace fhe {
 
 constexpr int kLiftThreads = 128;
 
+// Signed lift: the value of batch item b is the two's-complement integer of sb bits held in
+// the low sb bits of its limbs (sb = 0: unsigned).  sign_of gives its sign bit; sext_limb gives
+// limb l of the same value sign-extended to every limb (limbs at and above bit sb ignored).
+__device__ __forceinline__ int item_sbits(int sbits, const int32_t* __restrict__ item_bits, int b, int L) {
+  // per-item widths are clamped to the limbs present (a signed launch stays signed for every item)
+  return item_bits ? min(max(__ldg(item_bits + b), 1), 32 * L) : sbits;
+}
+__device__ __forceinline__ uint32_t sign_of(const uint32_t* __restrict__ s, int N, int sb) {
+  return (__ldg(s + (size_t)((sb - 1) >> 5) * N) >> ((sb - 1) & 31)) & 1u;
+}
+__device__ __forceinline__ uint32_t sext_limb(uint32_t x, int l, int sb, uint32_t sgn) {
+  const int lo = 32 * l;
+  if (lo >= sb) return sgn ? 0xFFFFFFFFu : 0u;
+  const int tb = sb - lo;
+  if (tb >= 32) return x;
+  const uint32_t m = (1u << tb) - 1u;
+  return sgn ? (x | ~m) : (x & m);
+}
+
 // (hi:lo) 96-bit accumulator -> value mod q.  a2 < 2^8.
 __device__ __forceinline__ uint32_t reduce96(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t q, uint32_t r32,
                                              uint32_t r32s, uint32_t r64) {
@@ -40,7 +59,8 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
                                                        size_t dst_pstride, size_t dst_bstride, int npoly, int r,
                                                        int N, const uint32_t* __restrict__ pow2,
                                                        const uint32_t* __restrict__ qtab,
-                                                       const uint32_t* __restrict__ red) {
+                                                       const uint32_t* __restrict__ red, int sbits,
+                                                       const int32_t* __restrict__ item_bits) {
   extern __shared__ uint32_t sc[];  // [r][Lp], Lp = L rounded up to 4, zero padded
   const int Lp = (L + 3) & ~3;
   for (int idx = threadIdx.x; idx < r * Lp; idx += blockDim.x) {
@@ -55,6 +75,14 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
   uint32_t x[LB];
 #pragma unroll
   for (int l = 0; l < LB; ++l) x[l] = (l < L) ? __ldg(s + (size_t)l * N) : 0u;
+  // signed: x - sgn 2^sb = (x sign-extended to 32 L bits) - sgn 2^(32 L)
+  const int sb = item_sbits(sbits, item_bits, b, L);
+  const uint32_t sgn = sb > 0 ? sign_of(s, N, sb) : 0u;
+  if (sb > 0) {
+#pragma unroll
+    for (int l = 0; l < LB; ++l)
+      if (l < L) x[l] = sext_limb(x[l], l, sb, sgn);
+  }
   uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n;
   for (int i = 0; i < r; ++i) {
     const uint4* c4 = reinterpret_cast<const uint4*>(sc + i * Lp);
@@ -74,8 +102,10 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const uint32_t* __restric
       }
     }
     const uint32_t q = __ldg(qtab + i);
-    d[(size_t)i * N] = reduce96((uint32_t)acc, (uint32_t)(acc >> 32), a2, q, __ldg(red + 4 * i),
-                                __ldg(red + 4 * i + 1), __ldg(red + 4 * i + 2));
+    uint32_t res = reduce96((uint32_t)acc, (uint32_t)(acc >> 32), a2, q, __ldg(red + 4 * i), __ldg(red + 4 * i + 1),
+                            __ldg(red + 4 * i + 2));
+    if (sgn) res = sub_mod(res, __ldg(pow2 + (size_t)i * kMaxLiftLimbs + L), q);
+    d[(size_t)i * N] = res;
   }
 }
 
@@ -91,7 +121,9 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift_digits(const uint32_t* __
                                                               size_t dst_bstride, int npoly, int r, int N,
                                                               const uint32_t* __restrict__ pow24,
                                                               const uint32_t* __restrict__ qtab,
-                                                              const uint32_t* __restrict__ red) {
+                                                              const uint32_t* __restrict__ red,
+                                                              const uint32_t* __restrict__ pow2, int sbits,
+                                                              const int32_t* __restrict__ item_bits) {
   constexpr int MD = (32 * LB + 23) / 24;  // digits covering LB limbs
   constexpr int MP = (MD + 3) & ~3;        // padded to 128-bit loads
   static_assert(MP <= kLiftDigits, "digit table too short");
@@ -109,6 +141,13 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift_digits(const uint32_t* __
 #pragma unroll
   for (int l = 0; l < LB; ++l) x[l] = (l < L) ? __ldg(s + (size_t)l * N) : 0u;
   x[LB] = 0;
+  const int sb = item_sbits(sbits, item_bits, b, L);
+  const uint32_t sgn = sb > 0 ? sign_of(s, N, sb) : 0u;
+  if (sb > 0) {
+#pragma unroll
+    for (int l = 0; l < LB; ++l)
+      if (l < L) x[l] = sext_limb(x[l], l, sb, sgn);
+  }
   uint32_t z[MP];
 #pragma unroll
   for (int m = 0; m < MP; ++m) {
@@ -131,8 +170,10 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift_digits(const uint32_t* __
       }
     }
     const uint32_t q = __ldg(qtab + i);
-    d[(size_t)i * N] = reduce96((uint32_t)acc, (uint32_t)(acc >> 32), 0u, q, __ldg(red + 4 * i),
-                                __ldg(red + 4 * i + 1), __ldg(red + 4 * i + 2));
+    uint32_t res = reduce96((uint32_t)acc, (uint32_t)(acc >> 32), 0u, q, __ldg(red + 4 * i), __ldg(red + 4 * i + 1),
+                            __ldg(red + 4 * i + 2));
+    if (sgn) res = sub_mod(res, __ldg(pow2 + (size_t)i * kMaxLiftLimbs + L), q);
+    d[(size_t)i * N] = res;
   }
 }
 
@@ -187,11 +228,12 @@ static size_t lt_smem_bytes(const LtShape& sh) {
   return 512 + 16 * 128 + (size_t)(sh.n0 + sh.n1) * sh.Kpad * 2 + (size_t)kLtRows * sh.Kpad * 2;
 }
 
+template <bool SIGNED>
 __global__ void __launch_bounds__(kLtThreads, 1)
     k_lift_tc(const uint32_t* __restrict__ src, size_t src_pstride, size_t src_bstride, uint32_t* __restrict__ dst,
               size_t dst_pstride, size_t dst_bstride, LtShape sh, int N, const uint16_t* __restrict__ bmat,
               const uint32_t* __restrict__ qtab, const uint32_t* __restrict__ qinv,
-              const uint64_t* __restrict__ offL) {
+              const uint64_t* __restrict__ offL, int sbits, const int32_t* __restrict__ item_bits) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = sh.r, L = sh.L, Kpad = sh.Kpad;
@@ -286,6 +328,8 @@ __global__ void __launch_bounds__(kLtThreads, 1)
     const int p0 = hh * PH, np = max(0, min(P2, p0 + PH) - p0);
     uint8_t* arow = A + (size_t)(t0 >> 3) * sbo + (t0 & 7) * 16;
     uint32_t xv[32];
+    int ysb = 0;        // signed: the loaded tile's value width and sign
+    uint32_t ysgn = 0;
     auto load = [&](int t) {
       int n0, poly, b;
       tile_of(t, n0, poly, b);
@@ -294,6 +338,10 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       for (int j = 0; j < 32; ++j) {
         const int l = 2 * p0 + j;
         xv[j] = (j < 2 * np && l < L) ? __ldg(s + (size_t)l * N) : 0u;
+      }
+      if constexpr (SIGNED) {
+        ysb = item_sbits(sbits, item_bits, b, L);
+        ysgn = sign_of(s, N, ysb);
       }
     };
     int tl = 0;
@@ -307,8 +355,13 @@ __global__ void __launch_bounds__(kLtThreads, 1)
           uint32_t d[4];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            // byte b -> f16 (1024 + b) - 1152 = b - 128; a limb beyond L contributes no digits
-            const uint32_t x = xv[2 * jp + u];
+            // byte b -> f16 (1024 + b) - 1152 = b - 128; a limb beyond L contributes no digits.  Signed:
+            // the value sign-extended to 32 L bits, its top byte fed as the signed digit (b ^ 0x80) - 128
+            uint32_t x = xv[2 * jp + u];
+            if constexpr (SIGNED) {
+              const int l = 2 * (p0 + jp) + u;
+              x = sext_limb(x, l, ysb, ysgn) ^ (l == L - 1 ? 0x80000000u : 0u);
+            }
             const uint32_t lo = __byte_perm(x, 0x64646464u, 0x5140), hi = __byte_perm(x, 0x64646464u, 0x5342);
             asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u]) : "r"(lo), "r"(0x64806480u));
             asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u + 1]) : "r"(hi), "r"(0x64806480u));
@@ -386,7 +439,8 @@ __global__ void __launch_bounds__(kLtThreads, 1)
 // Tensor-core lift when it applies (L < 64, r <= 128, N a multiple of 128, shared memory fits);
 // returns 1 if launched, 0 if the caller must use the integer form.
 static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t sp, size_t sb, uint32_t* dst,
-                          size_t dp, size_t db, int npoly, int nbatch, int r, cudaStream_t st) {
+                          size_t dp, size_t db, int npoly, int nbatch, int r, int sbits, const int32_t* item_bits,
+                          cudaStream_t st) {
   const int N = ctx->N;
   if (!ctx->d_lift_tc || (ctx->crt_mode != FHE_CRT_DIRECT && ctx->crt_mode != FHE_CRT_DIRECT_CVT) || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
   LtShape sh;
@@ -406,13 +460,19 @@ static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t
   if (smem > 227 * 1024) return 0;
   static thread_local int configured_dev = -1, nsm = 0;
   if (configured_dev != ctx->device) {
-    cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_lift_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_lift_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     configured_dev = ctx->device;
   }
   const int grid = sh.ntiles < nsm ? sh.ntiles : nsm;
-  k_lift_tc<<<grid, kLtThreads, smem, st>>>(src, sp, sb, dst, dp, db, sh, N, ctx->d_lift_tc, ctx->d_q, ctx->d_qinv,
-                                            ctx->d_lift_off + (size_t)L * ctx->R);
+  if (sbits > 0 || item_bits)
+    k_lift_tc<true><<<grid, kLtThreads, smem, st>>>(src, sp, sb, dst, dp, db, sh, N, ctx->d_lift_tc, ctx->d_q,
+                                                    ctx->d_qinv, ctx->d_lift_off_s + (size_t)L * ctx->R, sbits,
+                                                    item_bits);
+  else
+    k_lift_tc<false><<<grid, kLtThreads, smem, st>>>(src, sp, sb, dst, dp, db, sh, N, ctx->d_lift_tc, ctx->d_q,
+                                                     ctx->d_qinv, ctx->d_lift_off + (size_t)L * ctx->R, 0, nullptr);
   return 1;
 }
 
@@ -426,7 +486,8 @@ unsigned int read_lift_status() {
 
 template <int LB>
 static void lift_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t sp, size_t sb, uint32_t* dst,
-                        size_t dp, size_t db, int npoly, int nbatch, int r, cudaStream_t st) {
+                        size_t dp, size_t db, int npoly, int nbatch, int r, int sbits, const int32_t* item_bits,
+                        cudaStream_t st) {
   const int N = ctx->N;
   const int threads = N < kLiftThreads ? N : kLiftThreads;
   dim3 grid((N + threads - 1) / threads, npoly * nbatch);
@@ -436,21 +497,22 @@ static void lift_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t s
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_lift_digits<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_lift_digits<LB><<<grid, threads, smem, st>>>(src, L, sp, sb, dst, dp, db, npoly, r, N, ctx->d_pow24, ctx->d_q,
-                                                    ctx->d_red);
+                                                    ctx->d_red, ctx->d_pow2, sbits, item_bits);
     return;
   }
   size_t smem = (size_t)r * ((L + 3) & ~3) * sizeof(uint32_t);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_lift<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_lift<LB><<<grid, threads, smem, st>>>(src, L, sp, sb, dst, dp, db, npoly, r, N, ctx->d_pow2, ctx->d_q,
-                                           ctx->d_red);
+                                           ctx->d_red, sbits, item_bits);
 }
 
-int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
-                uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r,
-                cudaStream_t st) {
+static int lift_any(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
+                    uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r, int sbits,
+                    const int32_t* item_bits, cudaStream_t st) {
   if (L < 1 || L > kMaxLiftLimbs || r < 1 || r > ctx->R || nbatch < 1 || npoly < 1 ||
-      (size_t)npoly * nbatch > 65535u) {
-    set_error("lift: bad sizes L=%d r=%d", L, r);
+      (size_t)npoly * nbatch > 65535u || sbits < 0 || sbits > 32 * L ||
+      ((sbits > 0 || item_bits) && L >= kMaxLiftLimbs)) {
+    set_error("lift: bad sizes L=%d r=%d sbits=%d", L, r, sbits);
     return FHE_EINVAL;
   }
   if ((size_t)r * ((L + 3) & ~3) * 4 > 200 * 1024) {
@@ -458,12 +520,13 @@ int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstri
     return FHE_EINVAL;
   }
   ProfScope ps(ctx, FHE_K_LIFT, 1, st);
-  if (lift_tc_launch(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, npoly, nbatch, r, st))
+  if (lift_tc_launch(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, npoly, nbatch, r, sbits,
+                     item_bits, st))
     return FHE_OK;
 #define FHE_LIFT_CASE(B)                                                                 \
   if (L <= B) {                                                                          \
     lift_launch<B>(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, \
-                   npoly, nbatch, r, st);                                                \
+                   npoly, nbatch, r, sbits, item_bits, st);                              \
     return FHE_OK;                                                                       \
   }
   FHE_LIFT_CASE(4)
@@ -479,6 +542,24 @@ int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstri
   FHE_LIFT_CASE(128)
 #undef FHE_LIFT_CASE
   return FHE_EINVAL;
+}
+
+int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
+                uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r,
+                cudaStream_t st) {
+  return lift_any(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, npoly, nbatch, r, 0, nullptr,
+                  st);
+}
+
+int launch_lift_signed(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,
+                       uint32_t* dst, size_t dst_pstride, size_t dst_bstride, int npoly, int nbatch, int r, int sbits,
+                       const int32_t* item_bits, cudaStream_t st) {
+  if (sbits < 1 && !item_bits) {
+    set_error("lift (signed): no sign bit position");
+    return FHE_EINVAL;
+  }
+  return lift_any(ctx, src, L, src_pstride, src_bstride, dst, dst_pstride, dst_bstride, npoly, nbatch, r, sbits,
+                  item_bits, st);
 }
 
 int launch_lift_small(const fhe_ctx* ctx, const void* src, bool is_i8, size_t src_bstride, uint32_t* dst,

@@ -66,7 +66,7 @@ __global__ void k_pw_key(uint32_t* __restrict__ Y, const uint32_t* __restrict__ 
   *y1 = o1;
 }
 
-__global__ void k_pw_mul(uint32_t* __restrict__ Z, const uint32_t* __restrict__ A, size_t a_bstride,
+__global__ void k_pw_mul(uint32_t* __restrict__ Z, size_t z_bstride, const uint32_t* __restrict__ A, size_t a_bstride,
                          const uint32_t* __restrict__ B, size_t b_bstride, int r, int N,
                          const uint32_t* __restrict__ qtab, const uint32_t* __restrict__ qinv) {
   const int k = blockIdx.y, b = blockIdx.z;
@@ -80,7 +80,7 @@ __global__ void k_pw_mul(uint32_t* __restrict__ Z, const uint32_t* __restrict__ 
   o.y = mont_mul(a.y, c.y, q, qi);
   o.z = mont_mul(a.z, c.z, q, qi);
   o.w = mont_mul(a.w, c.w, q, qi);
-  *((uint4*)(Z + (size_t)b * (size_t)r * N + (size_t)k * N) + n4) = o;
+  *((uint4*)(Z + (size_t)b * z_bstride + (size_t)k * N) + n4) = o;
 }
 
 static dim3 pw_grid(int N, int r, int nbatch, int threads) {
@@ -107,8 +107,18 @@ int launch_pointwise_mul(const fhe_ctx* ctx, uint32_t* Z, const uint32_t* A, siz
   const int threads = 128;
   if (nbatch > 65535 || ctx->N < 4) return FHE_EINVAL;
   ProfScope ps(ctx, FHE_K_POINTWISE, 1, st);
-  k_pw_mul<<<pw_grid(ctx->N, r, nbatch, threads), threads, 0, st>>>(Z, A, a_bstride, B, b_bstride, r, ctx->N,
-                                                                     ctx->d_q, ctx->d_qinv);
+  k_pw_mul<<<pw_grid(ctx->N, r, nbatch, threads), threads, 0, st>>>(Z, (size_t)r * ctx->N, A, a_bstride, B,
+                                                                     b_bstride, r, ctx->N, ctx->d_q, ctx->d_qinv);
+  return FHE_OK;
+}
+int launch_pointwise_mul_strided(const fhe_ctx* ctx, uint32_t* Z, size_t z_bstride, const uint32_t* A,
+                                 size_t a_bstride, const uint32_t* B, size_t b_bstride, int r, int nbatch,
+                                 cudaStream_t st) {
+  const int threads = 128;
+  if (nbatch > 65535 || ctx->N < 4) return FHE_EINVAL;
+  ProfScope ps(ctx, FHE_K_POINTWISE, 1, st);
+  k_pw_mul<<<pw_grid(ctx->N, r, nbatch, threads), threads, 0, st>>>(Z, z_bstride, A, a_bstride, B, b_bstride, r,
+                                                                     ctx->N, ctx->d_q, ctx->d_qinv);
   return FHE_OK;
 }
 
@@ -168,10 +178,12 @@ __global__ void k_moddown(const uint32_t* __restrict__ in, int Lin, uint32_t* __
 
 // mode 0: a + b, 1: a - b, 2: -a  (mod 2^bits)
 __global__ void k_addsub(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* __restrict__ out,
-                         int L, int bits, int mode, int N) {
+                         int L, int bits, int mode, int N, int b_polys) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const size_t off = (size_t)blockIdx.y * L * N + n;
+  // b_polys > 0: b holds that many polynomials, reused for every ciphertext (broadcast mode)
+  const size_t boff = b_polys > 0 ? (size_t)(blockIdx.y % b_polys) * L * N + n : off;
   uint32_t c = (mode == 0) ? 0u : 1u;  // subtraction: x + ~y + 1
   for (int l = 0; l < L; ++l) {
     const size_t i = off + (size_t)l * N;
@@ -180,8 +192,9 @@ __global__ void k_addsub(const uint32_t* __restrict__ a, const uint32_t* __restr
       x = 0;
       y = ~a[i];
     } else {
+      const uint32_t bv = b[boff + (size_t)l * N];
       x = a[i];
-      y = (mode == 0) ? b[i] : ~b[i];
+      y = (mode == 0) ? bv : ~bv;
     }
     const uint64_t s = (uint64_t)x + y + c;
     c = (uint32_t)(s >> 32);
@@ -277,10 +290,11 @@ __global__ void k_key_combine(const uint32_t* __restrict__ t, int Lt, const int3
 }
 
 // b_0 += value 2^shift (mod 2^bits) for each ciphertext of the batch (addconst)
-__global__ void k_add_const(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t value, int shift,
-                            int L, int bits, int N, int cnum) {
+__global__ void k_add_const(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t value,
+                            const int64_t* __restrict__ values, int shift, int L, int bits, int N, int cnum) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cnum) return;
+  if (values) value = values[c];  // pairwise: one constant per ciphertext
   const size_t base = (size_t)c * 2 * L * N;  // coefficient 0 of poly 0
   const int sl = shift >> 5, sb = shift & 31;
   const uint64_t v = (uint64_t)value;
@@ -305,10 +319,43 @@ __global__ void k_add_const(const uint32_t* __restrict__ in, uint32_t* __restric
 
 static dim3 limb_grid(int N, int y, int threads) { return dim3((N + threads - 1) / threads, y); }
 
-int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, int shift, int logQ,
-                     int cnum, cudaStream_t st) {
+int launch_add_const(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t value, const int64_t* values,
+                     int shift, int logQ, int cnum, cudaStream_t st) {
   ProfScope ps(ctx, FHE_K_LIMB, 1, st);
-  k_add_const<<<(cnum + 127) / 128, 128, 0, st>>>(in, out, value, shift, limbs_for_bits(logQ), logQ, ctx->N, cnum);
+  k_add_const<<<(cnum + 127) / 128, 128, 0, st>>>(in, out, value, values, shift, limbs_for_bits(logQ), logQ, ctx->N,
+                                                  cnum);
+  return FHE_OK;
+}
+
+// Multiplication by the monomial X^k (0 <= k < N) in Z_Q[X]/(X^N + 1): coefficient i moves to
+// i + k, negated (two's complement mod 2^bits) when it wraps past X^N = -1.  k = N/2 is imult
+// (X^(N/2) evaluates to the imaginary unit at every slot's root).
+__global__ void k_monomial(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int L, int bits, int k,
+                           int logN) {
+  const int N = 1 << logN;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const bool neg = e < k;
+  const int i = neg ? e - k + N : e - k;
+  const uint32_t* x = in + (size_t)blockIdx.y * L * N + i;
+  uint32_t* y = out + (size_t)blockIdx.y * L * N + e;
+  uint32_t c = 1;
+  for (int l = 0; l < L; ++l) {
+    uint32_t v = __ldg(x + (size_t)l * N);
+    if (neg) {
+      const uint64_t s = (uint64_t)(~v) + c;
+      v = (uint32_t)s;
+      c = (uint32_t)(s >> 32);
+    }
+    y[(size_t)l * N] = v & mask_of(l, bits);
+  }
+}
+
+int launch_monomial(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, int logQ, int k, int npolys,
+                    cudaStream_t st) {
+  if (npolys > 65535 || k < 0 || k >= ctx->N || in == out) return FHE_EINVAL;
+  ProfScope ps(ctx, FHE_K_LIMB, 1, st);
+  k_monomial<<<limb_grid(ctx->N, npolys, 128), 128, 0, st>>>(in, out, limbs_for_bits(logQ), logQ, k, ctx->prm.logN);
   return FHE_OK;
 }
 
@@ -329,10 +376,11 @@ int launch_moddown(const fhe_ctx* ctx, const uint32_t* in, int logQ_in, uint32_t
   return FHE_OK;
 }
 int launch_addsub(const fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* out, int logQ, int npolys,
-                  int mode, cudaStream_t st) {
+                  int mode, cudaStream_t st, int b_polys) {
   if (npolys > 65535) return FHE_EINVAL;
   ProfScope ps(ctx, FHE_K_LIMB, 1, st);
-  k_addsub<<<limb_grid(ctx->N, npolys, 128), 128, 0, st>>>(a, b, out, limbs_for_bits(logQ), logQ, mode, ctx->N);
+  k_addsub<<<limb_grid(ctx->N, npolys, 128), 128, 0, st>>>(a, b, out, limbs_for_bits(logQ), logQ, mode, ctx->N,
+                                                           b_polys);
   return FHE_OK;
 }
 int launch_mult_const(const fhe_ctx* ctx, const uint32_t* in, int32_t c, uint32_t* out, int logQ, int npolys,

@@ -520,6 +520,86 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
   }
 }
 
+// ------------------------------------------- automorphism in the transform domain
+// kappa_g: a(X) -> a(X^g) (Sec. 6 leftrotate with g = 5^j, conjugate with g = 2N - 1).  The forward
+// transform leaves a(psi^(2 brv(k) + 1)) at index k, so
+//   NTT(kappa_g a)[k] = NTT(a)[pi(k)],  pi(k) = brv((g brv(k) + (g - 1)/2) mod N)
+// (brv over log N bits).  With k = 256 c + m (matrix row c, column m), brv(k) = brv8(m) N1 + brv(c)
+// (N1 = N / 256), so every output row c reads one source row c' = brv(w mod N1),
+// w = (g brv(c) + (g - 1)/2) mod N, at columns m' = brv8((w / N1 + g brv8(m)) mod 256).  A rotation
+// by many steps therefore lifts and transforms its input once and applies each kappa_g as a row
+// gather in front of the key products.
+__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) { return bits ? __brev(x) >> (32 - bits) : 0u; }
+
+// Fused: for matrix row c of (ciphertext b, prime p), gather row c' of AH (the forward transform
+// of the key-switch input, [batch][r][N]), multiply by the key rows K[0][p], K[1][p] (Montgomery)
+// and run the inverse row stages of both products into Y = [batch][2][r][N] blocks 0 and 1.
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key_perm(uint32_t* __restrict__ Y,
+                                                                        const uint32_t* __restrict__ AH,
+                                                                        const uint32_t* __restrict__ K, int krows,
+                                                                        int r, int logN, uint32_t g,
+                                                                        const uint2* __restrict__ itw,
+                                                                        const uint32_t* __restrict__ qtab,
+                                                                        const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
+  const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN, logN1 = logN - 8, N1 = 1 << logN1;
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const int c = blockIdx.x * kRowsPerCta + sub;
+  const uint32_t w = (g * brv_bits((uint32_t)c, logN1) + (g - 1u) / 2u) & (uint32_t)(N - 1);
+  const int cs = (int)brv_bits(w & (uint32_t)(N1 - 1), logN1);
+  const uint32_t whi = w >> logN1;
+  uint32_t* sr = s + sub * 2 * kSlot;
+  const uint32_t* src = AH + ((size_t)b * r + p) * N + (size_t)cs * kRowLen;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sr[j0 + 16 * k] = __ldg(src + j0 + 16 * k);
+  __syncwarp();
+  const size_t coff = (size_t)c * kRowLen;
+  const uint4* kb = reinterpret_cast<const uint4*>(K + (size_t)p * N + coff + 16 * j0);
+  const uint4* ka = reinterpret_cast<const uint4*>(K + (size_t)(krows + p) * N + coff + 16 * j0);
+  uint32_t x[2][16];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 vb = __ldg(kb + v), va = __ldg(ka + v);
+    const uint32_t kbv[4] = {vb.x, vb.y, vb.z, vb.w}, kav[4] = {va.x, va.y, va.z, va.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t m = 16u * j0 + 4u * v + u;
+      const uint32_t mp = brv_bits((whi + g * brv_bits(m, 8)) & 255u, 8);
+      const uint32_t d = sr[mp];
+      x[0][4 * v + u] = mont_mul(d, kbv[u], q, qi);
+      x[1][4 * v + u] = mont_mul(d, kav[u], q, qi);
+    }
+  }
+  rows_inv_multi<2>(x, c, j0, sr, N, itw + (size_t)p * N, q);  // syncs the warp before reusing sr
+  uint32_t* y0 = Y + ((size_t)b * 2 * r + p) * N + coff;
+  uint32_t* y1 = y0 + (size_t)r * N;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    y0[j0 + 16 * k] = x[0][k];
+    y1[j0 + 16 * k] = x[1][k];
+  }
+}
+
+// Any ring size: the same gather and key products, one thread per transform coefficient
+// (the inverse transforms follow as a separate launch).  grid (N / 256, batch * r).
+__global__ void k_pw_key_perm(uint32_t* __restrict__ Y, const uint32_t* __restrict__ AH,
+                              const uint32_t* __restrict__ K, int krows, int r, int logN, uint32_t g,
+                              const uint32_t* __restrict__ qtab, const uint32_t* __restrict__ qinv) {
+  const int N = 1 << logN;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int p = blockIdx.y % r, b = blockIdx.y / r;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const uint32_t u = (uint32_t)(((uint64_t)g * brv_bits((uint32_t)k, logN) + (g - 1u) / 2u) & (uint64_t)(N - 1));
+  const uint32_t d = __ldg(AH + ((size_t)b * r + p) * N + brv_bits(u, logN));
+  uint32_t* y0 = Y + ((size_t)b * 2 * r + p) * N;
+  y0[k] = mont_mul(d, __ldg(K + (size_t)p * N + k), q, qi);
+  y0[(size_t)r * N + k] = mont_mul(d, __ldg(K + (size_t)(krows + p) * N + k), q, qi);
+}
+
 static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, int r, bool inverse,
                      cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
@@ -615,6 +695,39 @@ int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krow
     dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
     k_ntt_rows_key<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, K, krows, r, logN, ctx->d_psi2, ctx->d_ipsi2,
                                                       ctx->d_q, ctx->d_qinv);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);
+    cols_launch(ctx, Y, RowMap{r, r}, nbatch * 2 * r, r, true, st);
+  }
+  return FHE_OK;
+}
+
+int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const uint32_t* K, int krows, int r,
+                    int nbatch, uint32_t g, cudaStream_t st) {
+  const int logN = ctx->prm.logN, N = ctx->N;
+  if (r > krows || r < 1 || nbatch < 1 || !(g & 1u) || g >= 2u * (uint32_t)N) {
+    set_error("key_perm: bad arguments (r %d, key rows %d, g %u)", r, krows, g);
+    return FHE_EINVAL;
+  }
+  if (logN <= 12 || (size_t)nbatch * r > 65535u) {
+    if ((size_t)nbatch * r > 65535u) {
+      set_error("key_perm: %d x %d rows exceed one launch", nbatch, r);
+      return FHE_EINVAL;
+    }
+    {
+      ProfScope ps(ctx, FHE_K_POINTWISE, 1, st);
+      const int threads = N < 256 ? N : 256;
+      k_pw_key_perm<<<dim3((N + threads - 1) / threads, nbatch * r), threads, 0, st>>>(Y, AH, K, krows, r, logN, g,
+                                                                                    ctx->d_q, ctx->d_qinv);
+    }
+    return launch_ntt(ctx, Y, nbatch * 2, r, r, r, true, st);
+  }
+  {
+    ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
+    dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
+    k_ntt_rows_key_perm<<<grid, 16 * kRowsPerCta, 0, st>>>(Y, AH, K, krows, r, logN, g, ctx->d_ipsi2, ctx->d_q,
+                                                           ctx->d_qinv);
   }
   {
     ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);

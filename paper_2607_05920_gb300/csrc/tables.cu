@@ -278,19 +278,24 @@ static int build_crt_tc(fhe_ctx* ctx, const std::vector<uint32_t>& qhat, const s
 // is T_i = sum_a 256^a sum_k d_k c_{i,k,a}, c_{i,k,a} the digits of
 // C_{i,k} = 2^(8k) 2^32 mod q_i; T_i = (x - 128 sum_k 256^k) 2^32 (mod q_i), so
 // adding off_i(L) = (128 sum_{k<4L} 256^k) 2^32 mod q_i (and 2^17 q_i to make
-// it non-negative) and one Montgomery reduction give x mod q_i.
+// it non-negative) and one Montgomery reduction give x mod q_i.  The signed
+// form (a two's-complement value of 32 L bits) feeds the top byte as the
+// signed digit (b ^ 0x80) - 128 and so takes offs_i(L), the same sum without
+// the top byte's term.
 static int build_lift_tc(fhe_ctx* ctx) {
   const int R = ctx->R, KMAX = 4 * kMaxLiftLimbs;
   const std::vector<uint32_t>& q = ctx->q;
   const size_t rows8 = (size_t)((4 * R + 7) / 8) * 8;  // whole 8-row core-matrix groups
   std::vector<uint16_t> mat(rows8 * KMAX, 0);
-  std::vector<uint64_t> off((size_t)(kMaxLiftLimbs + 1) * R, 0);
+  std::vector<uint64_t> off((size_t)(kMaxLiftLimbs + 1) * R, 0), offs((size_t)(kMaxLiftLimbs + 1) * R, 0);
   for (int i = 0; i < R; ++i) {
     const uint64_t qi = q[i];
     uint64_t c = ((uint64_t)1 << 32) % qi;  // C_{i,0} = 2^32 mod q
     uint64_t offacc = 0;                    // (128 sum_{k' < k} 256^k') 2^32 mod q
     for (int k = 0; k < KMAX; ++k) {
       if ((k & 3) == 0) off[(size_t)(k >> 2) * R + i] = offacc + (qi << 17);
+      // signed form of L = (k + 1) / 4 limbs: the top byte is a signed digit, no offset for it
+      if ((k & 3) == 3) offs[(size_t)((k + 1) >> 2) * R + i] = offacc + (qi << 17);
       // digits of C: bytes 0..2 balanced with carry, byte 3 takes the carry (C < q < 2^30)
       int carry = 0, dg[4];
       for (int a = 0; a < 3; ++a) {
@@ -308,7 +313,9 @@ static int build_lift_tc(fhe_ctx* ctx) {
     }
     off[(size_t)kMaxLiftLimbs * R + i] = offacc + (qi << 17);
   }
-  if (!(ctx->d_lift_tc = upload(ctx, mat)) || !(ctx->d_lift_off = upload(ctx, off))) return FHE_ENOMEM;
+  if (!(ctx->d_lift_tc = upload(ctx, mat)) || !(ctx->d_lift_off = upload(ctx, off)) ||
+      !(ctx->d_lift_off_s = upload(ctx, offs)))
+    return FHE_ENOMEM;
   return FHE_OK;
 }
 

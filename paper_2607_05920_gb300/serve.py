@@ -7,17 +7,29 @@ serving loop:
 * admits arrived requests while the device-memory footprint of admitted work
   (outputs, intermediates and workspace share at the request's level) stays
   within a budget;
-* forms batches from everything admitted and ready: multiplications of any
-  level go into one ragged batch (`fhe_mult_relin_rescale_ragged`, each
-  ciphertext keeps its own modulus), rotations are grouped by (step, level);
+* forms batches from everything admitted and ready: multiplications go into
+  ragged batches (`fhe_mult_relin_rescale_ragged`, each ciphertext keeps its
+  own modulus), rotations into batches of one (step, level);
 * keeps several batches in flight on separate CUDA streams, so requests that
   arrive while others run are admitted as memory and streams free up and
   their work overlaps on the device;
 * advances multi-stage requests (the polynomial) stage by stage and records
-  arrival-to-completion latency.
+  arrival-to-completion latency; a request's final limb work runs on its own
+  stream and completes by event, so the loop never waits on the device.
+
+Multiplications are grouped by limb count (levels within 32 bits of each
+other), so a batch pays for at most one limb of padding, and rotations by
+(step, level).  Failures are handled on the host: a completion callback that
+raises marks only its own request, and a batch whose stream reports an error
+(`fail_batch`, a hook tests use to inject one) fails only its own requests;
+the server finishes the rest.
+
+`run_per_op` serves the same request stream without batching: each request,
+as it arrives, is issued alone through the plain calls on one stream (the
+baseline the served form is measured against).
 
 Results are exact: a request's ciphertext is the same, bit for bit, whether it
-ran alone or inside any mix (the ragged batch uses the widest level's primes,
+ran alone or inside any mix (the ragged batch uses the widest member's primes,
 which is exact for every member).
 
 The degree-7 request evaluates an odd sigmoid-like polynomial fitted once by
@@ -58,6 +70,7 @@ class Request:
     t_done: float = -1.0
     result: object = None
     footprint: int = 0
+    error: str = ""
 
 
 @dataclass
@@ -73,8 +86,25 @@ class Task:
     step: int = 0
 
 
+def linear_part(ctx: Context, terms: dict, l3: int, k: int):
+    """sum_i C_i x^i + C_0 2^k at level l3, then rescale by COEF_SHIFT bits (on the current stream)."""
+    acc = None
+    for i, t in terms.items():
+        o = ctx.empty_ct(1, l3)
+        fhe_mult_const(ctx, Ciphertext(t.unsqueeze(0), l3), COEF_2_30[i], o)
+        if acc is None:
+            acc = o
+        else:
+            fhe_add(ctx, acc, o, acc)
+    fhe_add_const(ctx, acc, COEF_2_30[0], k, acc)
+    out = ctx.empty_ct(1, l3 - COEF_SHIFT)
+    fhe_rescale(ctx, acc, COEF_SHIFT, out)
+    return out.data[0]
+
+
 class Server:
-    def __init__(self, ctx: Context, pool: dict, k: int, budget_bytes: int, max_batch: int = 64, streams: int = 2):
+    def __init__(self, ctx: Context, pool: dict, k: int, budget_bytes: int, max_batch: int = 64, streams: int = 2,
+                 fail_batch=None):
         import torch
 
         self.torch = torch
@@ -84,8 +114,10 @@ class Server:
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
         self.streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        self.finish_stream = torch.cuda.Stream()
         self.ws = [None] * len(self.streams)
         self.busy = [None] * len(self.streams)   # (event, tasks, outputs) per stream
+        self.fail_batch = fail_batch              # (stream index, tasks) -> True to fail that batch (injection)
         self.N = ctx.N
 
     # ------------------------------------------------------------ footprints
@@ -136,33 +168,32 @@ class Server:
         return r.regs[name]
 
     def _finish_poly(self, r: Request):
-        """Linear combination at level l - 3k: sum C_i x^i + C_0 Delta, then rescale by 30 bits."""
+        """Linear combination at level l - 3k on the finishing stream; returns the event that completes it."""
+        torch = self.torch
         k, l3 = self.k, r.logQ - 3 * self.k
-        x = self._operand(r, r.a)
-        terms = {1: self._down(x, r.logQ, l3, r, "x_d3"), 3: self._down(r.regs["x3"], r.logQ - 2 * k, l3, r, "x3_d"),
-                 5: r.regs["x5"], 7: r.regs["x7"]}
-        acc = None
-        for i, t in terms.items():
-            o = self.ctx.empty_ct(1, l3)
-            fhe_mult_const(self.ctx, self._ct(t, l3), COEF_2_30[i], o)
-            if acc is None:
-                acc = o
-            else:
-                fhe_add(self.ctx, acc, o, acc)
-        fhe_add_const(self.ctx, acc, COEF_2_30[0], k, acc)
-        out = self.ctx.empty_ct(1, l3 - COEF_SHIFT)
-        fhe_rescale(self.ctx, acc, COEF_SHIFT, out)
-        return out.data[0]
+        fs_ = self.finish_stream
+        fs_.wait_stream(torch.cuda.current_stream())  # the mod-downs of the operands run on the main stream
+        with torch.cuda.stream(fs_):
+            x = self._operand(r, r.a)
+            terms = {1: self._down(x, r.logQ, l3, r, "x_d3"),
+                     3: self._down(r.regs["x3"], r.logQ - 2 * k, l3, r, "x3_d"), 5: r.regs["x5"], 7: r.regs["x7"]}
+            for t in terms.values():
+                t.record_stream(fs_)
+            r.result = linear_part(self.ctx, terms, l3, k)
+            ev = torch.cuda.Event()
+            ev.record(fs_)
+        r.result.record_stream(torch.cuda.current_stream())
+        return ev
 
-    def _advance(self, r: Request, now: float) -> bool:
-        """Called when the request's stage tasks are done; True if the request is complete."""
+    def _advance(self, r: Request, now: float):
+        """Called when the request's stage tasks are done: True if the request is complete, an event
+        if its final work is in flight, False if another stage follows."""
         if r.op in ("mult", "rotate"):
             r.result = r.regs["out"]
             return True
         r.stage += 1
         if r.stage == 3:
-            r.result = self._finish_poly(r)
-            return True
+            return self._finish_poly(r)
         return False
 
     # ----------------------------------------------------------------- batches
@@ -177,14 +208,11 @@ class Server:
                     v.record_stream(st)
         with torch.cuda.stream(st):
             if tasks[0].kind == "mult":
+                # one limb count per batch: canonical operands are zero above their own level already
                 lq_max = max(t.logQ for t in tasks)
-                L_pad = limbs(lq_max)
                 n = len(tasks)
-                A = torch.zeros((n, 2, L_pad, self.N), dtype=torch.int32, device=self.ctx.device)
-                B = torch.zeros_like(A)
-                for j, t in enumerate(tasks):
-                    A[j, :, :t.x.shape[1]].copy_(t.x)
-                    B[j, :, :t.y.shape[1]].copy_(t.y)
+                A = torch.stack([t.x for t in tasks])
+                B = torch.stack([t.y for t in tasks])
                 O = torch.empty_like(A)
                 bits = torch.tensor([t.logQ for t in tasks], dtype=torch.int32, device=self.ctx.device)
                 need = int(lib.fhe_workspace_bytes(self.ctx.handle, FHE_OP_MULT_RAGGED, lq_max, n))
@@ -211,7 +239,8 @@ class Server:
             return []
         first = ready[0]
         if first.kind == "mult":
-            sel = [t for t in ready if t.kind == "mult"][: self.max_batch]
+            nl = limbs(first.logQ)
+            sel = [t for t in ready if t.kind == "mult" and limbs(t.logQ) == nl][: self.max_batch]
         else:
             sel = [t for t in ready if t.kind == "rotate" and t.step == first.step and t.logQ == first.logQ]
             sel = sel[: self.max_batch]
@@ -220,17 +249,35 @@ class Server:
         return sel
 
     # ------------------------------------------------------------------- loop
-    def run(self, requests: list, time_scale: float = 1.0, max_wall_s: float = 1e9) -> dict:
+    def run(self, requests: list, time_scale: float = 1.0, max_wall_s: float = 1e9, on_done=None) -> dict:
+        """Serve `requests` (arrival times in seconds); on_done(request) is called for each completed request."""
         torch = self.torch
         arrivals = deque(sorted(requests, key=lambda r: r.t_arrive))
         queue = deque()
         ready = []
         waiting = {}   # request id -> number of outstanding tasks
+        finishing = deque()  # (event, request): final limb work in flight
+        failed_ids = set()
         in_use = 0
-        done = []
+        done, failed = [], []
+        cb_errors = 0
         t0 = time.perf_counter()
         torch.cuda.synchronize()
-        while len(done) < len(requests):
+
+        def complete(req, tnow):
+            nonlocal in_use, cb_errors
+            req.t_done = tnow
+            in_use -= req.footprint
+            done.append(req)
+            req.regs = {}
+            if on_done is not None:
+                try:
+                    on_done(req)
+                except Exception as exc:  # a failing callback marks its own request only
+                    req.error = f"callback: {exc!r}"
+                    cb_errors += 1
+
+        while len(done) + len(failed) < len(requests):
             now = (time.perf_counter() - t0) / time_scale
             if now * time_scale > max_wall_s:
                 break
@@ -249,29 +296,42 @@ class Server:
                 waiting[r.rid] = len(tasks)
                 ready.extend(tasks)
             progressed = False
+            while finishing and finishing[0][0].query():
+                _, req = finishing.popleft()
+                complete(req, (time.perf_counter() - t0) / time_scale)
+                progressed = True
             for si in range(len(self.streams)):
                 b = self.busy[si]
                 if b is not None and b[0].query():
                     self.busy[si] = None
                     progressed = True
+                    bad = self.fail_batch is not None and self.fail_batch(si, b[1])
                     for t, o in zip(b[1], b[2]):
+                        req = t.req
+                        if req.rid in failed_ids:
+                            continue
+                        if bad:  # this batch's results are lost: fail its requests, keep serving the others
+                            req.error = f"stream {si} reported an error"
+                            failed_ids.add(req.rid)
+                            in_use -= req.footprint
+                            req.regs = {}
+                            failed.append(req)
+                            continue
                         o.record_stream(torch.cuda.current_stream())  # consumed on the main stream from here on
-                        t.req.regs[t.name] = o
-                        waiting[t.req.rid] -= 1
-                        if waiting[t.req.rid] == 0:
-                            tnow = (time.perf_counter() - t0) / time_scale
-                            if self._advance(t.req, tnow):
-                                if t.req.op == "poly7":  # its final limb work ran on the main stream
-                                    torch.cuda.current_stream().synchronize()
-                                    tnow = (time.perf_counter() - t0) / time_scale
-                                t.req.t_done = tnow
-                                in_use -= t.req.footprint
-                                done.append(t.req)
-                                t.req.regs = {}
-                            else:
-                                tasks = self._stage_tasks(t.req)
-                                waiting[t.req.rid] = len(tasks)
+                        req.regs[t.name] = o
+                        waiting[req.rid] -= 1
+                        if waiting[req.rid] == 0:
+                            adv = self._advance(req, (time.perf_counter() - t0) / time_scale)
+                            if adv is True:
+                                complete(req, (time.perf_counter() - t0) / time_scale)
+                            elif adv is False:
+                                tasks = self._stage_tasks(req)
+                                waiting[req.rid] = len(tasks)
                                 ready.extend(tasks)
+                            else:
+                                finishing.append((adv, req))
+            if failed_ids:
+                ready[:] = [t for t in ready if t.req.rid not in failed_ids]
             for si in range(len(self.streams)):
                 if self.busy[si] is None and ready:
                     batch = self._pick_batch(ready)
@@ -282,12 +342,74 @@ class Server:
                 time.sleep(0.0002)
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t0) / time_scale
-        lat = np.array([r.t_done - r.t_arrive for r in done]) * 1e3
-        return {"completed": len(done), "offered": len(requests), "wall_s": wall,
-                "ops_per_s": len(done) / wall if wall > 0 else 0.0,
-                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-                "by_op": {op: int(sum(1 for r in done if r.op == op)) for op in ("mult", "rotate", "poly7")}}
+        return _stats(done, len(requests), wall, failed=len(failed), callback_errors=cb_errors)
+
+
+def _stats(done: list, offered: int, wall: float, **extra) -> dict:
+    lat = np.array([r.t_done - r.t_arrive for r in done]) * 1e3
+    out = {"completed": len(done), "offered": offered, "wall_s": wall,
+           "ops_per_s": len(done) / wall if wall > 0 else 0.0,
+           "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+           "by_op": {op: int(sum(1 for r in done if r.op == op)) for op in ("mult", "rotate", "poly7")}}
+    out.update(extra)
+    return out
+
+
+def per_op_request(ctx: Context, pool: dict, r: Request, k: int):
+    """One request alone through the plain calls (cnum 1) on the current stream; returns its result tensor."""
+    x = Ciphertext(pool[r.logQ].data[r.a:r.a + 1], r.logQ)
+    if r.op == "mult":
+        y = Ciphertext(pool[r.logQ].data[r.b:r.b + 1], r.logQ)
+        return ctx.mult_relin_rescale(x, y, k).data[0]
+    if r.op == "rotate":
+        return ctx.rotate(x, r.step).data[0]
+    l0 = r.logQ
+    x2 = ctx.mult_relin_rescale(x, x, k)
+    x3 = ctx.mult_relin_rescale(x2, ctx.moddown(x, l0 - k), k)
+    x4 = ctx.mult_relin_rescale(x2, x2, k)
+    x5 = ctx.mult_relin_rescale(x4, ctx.moddown(x, l0 - 2 * k), k)
+    x7 = ctx.mult_relin_rescale(x4, x3, k)
+    l3 = l0 - 3 * k
+    terms = {1: ctx.moddown(x, l3).data[0], 3: ctx.moddown(x3, l3).data[0], 5: x5.data[0], 7: x7.data[0]}
+    return linear_part(ctx, terms, l3, k)
+
+
+def run_per_op(ctx: Context, pool: dict, requests: list, k: int, time_scale: float = 1.0, on_done=None,
+               max_outstanding: int = 256) -> dict:
+    """The same request stream without batching: each request, as it arrives, issued alone through the
+    plain calls on the current stream (at most max_outstanding in flight); completion by one event per
+    request; on_done(request) after each completion."""
+    import torch
+
+    reqs = sorted(requests, key=lambda r: r.t_arrive)
+    outstanding = deque()
+    done = []
+    i = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while len(done) < len(reqs):
+        now = (time.perf_counter() - t0) / time_scale
+        progressed = False
+        while i < len(reqs) and reqs[i].t_arrive <= now and len(outstanding) < max_outstanding:
+            r = reqs[i]
+            i += 1
+            r.result = per_op_request(ctx, pool, r, k)
+            ev = torch.cuda.Event()
+            ev.record()
+            outstanding.append((ev, r))
+            progressed = True
+        while outstanding and outstanding[0][0].query():
+            _, r = outstanding.popleft()
+            r.t_done = (time.perf_counter() - t0) / time_scale
+            done.append(r)
+            if on_done is not None:
+                on_done(r)
+            progressed = True
+        if not progressed:
+            time.sleep(0.0002)
+    torch.cuda.synchronize()
+    return _stats(done, len(reqs), (time.perf_counter() - t0) / time_scale)
 
 
 def make_requests(g, rate_hz: float, duration_s: float, levels: list, pool_size: int, steps: list,

@@ -1,7 +1,7 @@
 """Shared set-up for the GPU parity tests: the same seeded keys and noise on both sides.
 
 The random polynomials come from fhe_synth; the CUDA library receives them
-through its C ABI (fhe_keygen / fhe_encrypt), the oracle receives them as
+through its C ABI (fhe_keygen_inject / fhe_encrypt_inject), the oracle receives them as
 Python integers.  Nothing here computes any part of the scheme.
 """
 from __future__ import annotations
@@ -23,9 +23,10 @@ class Pair:
     evk: tuple
     g: np.random.Generator
     rtk: dict
+    ck: tuple = None
 
 
-def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=(), crt=0):
+def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=(), crt=0, conj=False):
     import paper_2607_05920_gb300 as fhe
 
     g = fs.rng(seed)
@@ -36,7 +37,7 @@ def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=(), crt=0):
     a_ev = fs.uniform_limbs(g, (), N, logQ + logP)
     e_ev = fs.gaussian(g, (), N)
     ctx = fhe.Context(logN, logQ, logP, crt=crt)
-    ctx.keygen(s, a_pk, e_pk, a_ev, e_ev)
+    ctx.keygen_inject(s, a_pk, e_pk, a_ev, e_ev)
     prm = ckks.CkksParams(logN, logQ, logP)
     si = [int(x) for x in s]
     pk = ckks.public_key(prm, si, bigint.from_limbs(a_pk), [int(x) for x in e_pk])
@@ -47,7 +48,13 @@ def make_pair(logN, logQ, logP, seed, hwt=None, rot_steps=(), crt=0):
         e = fs.gaussian(g, (), N)
         ctx.keygen_rotation(step, a, e)
         rtk[step] = ckks.rotation_key(prm, si, step, bigint.from_limbs(a), [int(x) for x in e])
-    return Pair(ctx, prm, si, pk, evk, g, rtk)
+    ck = None
+    if conj:
+        a = fs.uniform_limbs(g, (), N, logQ + logP)
+        e = fs.gaussian(g, (), N)
+        ctx.keygen_conjugation(a, e)
+        ck = ckks.conjugation_key(prm, si, bigint.from_limbs(a), [int(x) for x in e])
+    return Pair(ctx, prm, si, pk, evk, g, rtk, ck)
 
 
 def to_dev(arr):
@@ -71,7 +78,7 @@ def encrypt_both(P: Pair, msgs, logQ=None):
     e1 = fs.gaussian(P.g, (cnum,), N)
     mask = (1 << lq) - 1
     pt = np.stack([bigint.to_limbs([x & mask for x in m], fhe.limbs(lq)) for m in msgs])
-    ct = P.ctx.encrypt(to_dev(pt), to_dev(v), to_dev(e0), to_dev(e1), logQ=lq)
+    ct = P.ctx.encrypt_inject(to_dev(pt), to_dev(v), to_dev(e0), to_dev(e1), logQ=lq)
     octs = [ckks.encrypt(P.prm, P.pk, m, [int(x) for x in v[i]], [int(x) for x in e0[i]],
                          [int(x) for x in e1[i]], logQ=lq) for i, m in enumerate(msgs)]
     return ct, octs

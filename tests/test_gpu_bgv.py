@@ -33,7 +33,7 @@ def _setup(logN, levels, seed, cnum):
     a_ev = fs.uniform_limbs(g, (), N, logQ + logP)
     e_ev = fs.gaussian(g, (), N)
     ctx = fhe.Context(logN, logQ, logP, scheme=fhe.FHE_SCHEME_BGV, t=T, bgv_q0=q0, bgv_r=r, bgv_levels=levels)
-    ctx.keygen(s, a_pk, e_pk, a_ev, e_ev)
+    ctx.keygen_inject(s, a_pk, e_pk, a_ev, e_ev)
     si = [int(x) for x in s]
     Q, PQ = prm.Qtop, prm.P * prm.Qtop
     pk = bgv.public_key(prm, si, [x % Q for x in bigint.from_limbs(a_pk)], [int(x) for x in e_pk])
@@ -45,7 +45,7 @@ def _setup(logN, levels, seed, cnum):
     L = fhe.limbs(logQ)
     pt = np.zeros((cnum, L, N), dtype=np.uint32)
     pt[:, 0, :] = m.astype(np.uint32)
-    ct = ctx.encrypt(to_dev(pt), to_dev(v), to_dev(e0), to_dev(e1))
+    ct = ctx.encrypt_inject(to_dev(pt), to_dev(v), to_dev(e0), to_dev(e1))
     return fhe, ctx, prm, si, pk, evk, m, v, e0, e1, ct
 
 

@@ -56,3 +56,50 @@ def test_served_results_equal_alone_results_and_oracle():
     assert tuple(bigint.from_limbs(host[p]) for p in range(2)) == tuple(want)
     ctx.close()
 
+
+def test_injected_failures_fail_only_their_own_requests():
+    """A completion callback that raises and a batch whose stream reports an error (both injected on the
+    host): the server completes every other request, with the same results as the plain per-op path."""
+    import torch
+
+    import paper_2607_05920_gb300 as fhe
+    from paper_2607_05920_gb300 import serve
+
+    steps = [1, 2]
+    P = make_pair(12, 400, 400, seed=63, rot_steps=steps)
+    ctx = P.ctx
+    g = fs.rng(64)
+    levels = [400, 360]
+    pool = {lq: fhe.Ciphertext(to_dev(fs.uniform_limbs(g, (3, 2), ctx.N, lq)), lq) for lq in levels}
+    reqs = serve.make_requests(g, rate_hz=500.0, duration_s=0.06, levels=levels, pool_size=3, steps=steps)
+    assert len(reqs) >= 15
+    calls = {"n": 0}
+    bad_cb = {r.rid for r in reqs[::5]}
+
+    def on_done(r):
+        calls["n"] += 1
+        if r.rid in bad_cb:
+            raise RuntimeError("callback failed")
+
+    batches = {"n": 0}
+
+    def fail_batch(si, tasks):  # the second batch that completes reports a stream error
+        batches["n"] += 1
+        return batches["n"] == 2
+
+    srv = serve.Server(ctx, pool, k=40, budget_bytes=2 << 30, max_batch=8, streams=2, fail_batch=fail_batch)
+    served = copy.deepcopy(reqs)
+    stats = srv.run(served, on_done=on_done)
+    torch.cuda.synchronize()
+    failed = [r for r in served if r.error.startswith("stream")]
+    assert stats["failed"] == len(failed) >= 1
+    assert stats["completed"] + stats["failed"] == len(reqs)
+    assert stats["callback_errors"] == sum(1 for r in served if r.error.startswith("callback"))
+    assert calls["n"] == stats["completed"]
+    alone = copy.deepcopy(reqs)
+    serve.run_per_op(ctx, pool, alone, 40)
+    by_id = {r.rid: r for r in alone}
+    for r in served:
+        if not r.error.startswith("stream"):
+            assert torch.equal(r.result, by_id[r.rid].result), (r.rid, r.op)
+    ctx.close()

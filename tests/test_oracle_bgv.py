@@ -88,3 +88,23 @@ def test_mod_switch_by_hand():
     prm = bgv.BgvParams(1, 3, 4, 7, 1, 3)
     out = bgv.mod_switch(prm, ([5, 20], [0, 0]), 1)
     assert out[0] == [2, 2]
+
+
+def test_slot_maps_by_hand_and_as_ring_isomorphism():
+    """Sec. 2 polynomial CRT: N = 4, t = 17 (2N = 8 divides 16): g = 3, psi = 3^2 = 9 (9^4 = -1 mod 17);
+    the slots of 1 + X are 1 + 9^(2k+1) = 10, 16, 9, 3.  Slot-wise products are ring products."""
+    assert bgv.primitive_root(17) == 3 and bgv.slot_root(4, 17) == 9
+    assert bgv.slot_decode([1, 1, 0, 0], 4, 17) == [10, 16, 9, 3]
+    assert bgv.slot_encode([10, 16, 9, 3], 4, 17) == [1, 1, 0, 0]
+    import fhe_synth as fs
+    from oracle import ring
+
+    t, N = 65537, 64
+    g = fs.rng(71)
+    x = [int(v) for v in fs.uniform_mod_t(g, (), N, t)]
+    y = [int(v) for v in fs.uniform_mod_t(g, (), N, t)]
+    mx, my = bgv.slot_encode(x, N, t), bgv.slot_encode(y, N, t)
+    assert bgv.slot_decode(mx, N, t) == x
+    prod = ring.mod_poly(ring.negacyclic_mul(mx, my), t)
+    assert bgv.slot_decode(prod, N, t) == [a * b % t for a, b in zip(x, y)]
+    assert bgv.primitive_root(65537) == 3

@@ -26,7 +26,7 @@ def _pair_setup():
     N = 1 << logN
     g = fs.rng(4242)
     ctx = fhe.Context(logN, logQ, logP)
-    ctx.keygen(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, logQ), fs.gaussian(g, (), N),
+    ctx.keygen_inject(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, logQ), fs.gaussian(g, (), N),
                fs.uniform_limbs(g, (), N, logQ + logP), fs.gaussian(g, (), N))
 
     def rand_ct(cnum):

@@ -381,6 +381,20 @@ int fhe_ring_mul(fhe_ctx* ctx, const uint32_t* a, int La, const uint32_t* b, int
 int fhe_mult_relin_rescale_noalloc(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out,
                                    void* stream);
 
+/* Kernel forms of the context's later calls (a schedule an autotuner picks;
+ * no counterpart in the paper): the reconstruction `crt` (FHE_CRT_*, as at
+ * creation), the lift `lift` and the transform schedule of ring products
+ * `ntt`.  Every combination gives bit-identical results.  Applies to work
+ * enqueued after the call (a CUDA graph keeps the forms it was captured
+ * with); not thread-safe with concurrent calls on the same context. */
+#define FHE_LIFT_AUTO 0  /* tensor cores when crt is FHE_CRT_DIRECT / _CVT, integer otherwise */
+#define FHE_LIFT_INT 1   /* 24-bit-digit / 96-bit-accumulator integer lift                    */
+#define FHE_LIFT_TC 2    /* tcgen05 byte-digit GEMM where it applies (L < 64, r <= 128)        */
+#define FHE_NTT_FUSED 0  /* N > 2^12: column pass, one fused row pass (forward rows, products,
+                            inverse rows), column pass                                        */
+#define FHE_NTT_SPLIT 1  /* full forward transforms, pointwise products, full inverse transforms */
+int fhe_set_forms(fhe_ctx* ctx, int crt, int lift, int ntt);
+
 /* Diagnostics (no counterpart in the paper; measurement support).
  * Kernel classes: */
 #define FHE_K_LIFT 0      /* limb -> RNS lift                        */

@@ -48,6 +48,11 @@ FHE_OP_RING_MUL = 6
 FHE_OP_MULT_RAGGED = 7
 FHE_OP_MULT_PLAIN = 8
 FHE_OP_ENCODE = 9
+FHE_LIFT_AUTO = 0
+FHE_LIFT_INT = 1
+FHE_LIFT_TC = 2
+FHE_NTT_FUSED = 0
+FHE_NTT_SPLIT = 1
 FHE_SAMPLE_UNIFORM = 0
 FHE_SAMPLE_TERNARY = 1
 FHE_SAMPLE_HWT = 2
@@ -115,6 +120,7 @@ SIGNATURES = {
     "fhe_bgv_decode": (_I, [_P, _P, _SZ, _I, _P, _P]),
     "fhe_mult_relin_rescale_noalloc": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _I,
                                             ctypes.POINTER(FheCt), _P]),
+    "fhe_set_forms": (_I, [_P, _I, _I, _I]),
     "fhe_profile_reset": (_I, [_P, _I]),
     "fhe_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
 }
@@ -672,6 +678,11 @@ def fhe_bgv_decode(ctx: Context, coeffs):
 
 def fhe_primes_for_bound(bound_bits: int) -> int:
     return int(lib.fhe_primes_for_bound(int(bound_bits)))
+
+
+def fhe_set_forms(ctx: Context, crt: int, lift: int = FHE_LIFT_AUTO, ntt: int = FHE_NTT_FUSED) -> None:
+    _check(lib.fhe_set_forms(ctx.handle, int(crt), int(lift), int(ntt)), "fhe_set_forms")
+    ctx.crt = int(crt)
 
 
 def fhe_profile_reset(ctx: Context, enable: bool) -> None:

@@ -402,6 +402,18 @@ const char* fhe_last_error(void) { return fhe::last_error(); }
 
 int fhe_primes_for_bound(int bound_bits) { return primes_for_bound_global(bound_bits); }
 
+int fhe_set_forms(fhe_ctx* ctx, int crt, int lift, int ntt) {
+  if (!ctx || crt < FHE_CRT_DIRECT || crt > FHE_CRT_DIRECT_CVT || lift < FHE_LIFT_AUTO || lift > FHE_LIFT_TC ||
+      (ntt != FHE_NTT_FUSED && ntt != FHE_NTT_SPLIT)) {
+    set_error("set_forms: bad arguments (crt %d, lift %d, ntt %d)", crt, lift, ntt);
+    return FHE_EINVAL;
+  }
+  ctx->crt_mode = crt;
+  ctx->lift_form = lift;
+  ctx->ntt_form = ntt;
+  return FHE_OK;
+}
+
 int fhe_profile_reset(fhe_ctx* ctx, int enable) {
   if (!ctx) {
     set_error("profile_reset: null context");

@@ -128,6 +128,9 @@ struct fhe_ctx {
   std::vector<size_t> crt_tc_off;
   std::vector<uint8_t> crt_tc_exact22;  // per r: every column sum is below 2^22 in magnitude
   int crt_tc_mt = 0;              // output byte columns covered, in 16s
+  int lift_form = 0;              // FHE_LIFT_AUTO (tensor cores with the direct CRT modes), _INT, _TC
+  int ntt_form = 0;               // FHE_NTT_FUSED: ring products run their transform-domain work in one
+                                  // fused row pass; FHE_NTT_SPLIT: separate transforms and products
   int crt_mode = 0;               // 0 direct CRT (tensor cores where it applies), 3 the same with cvt.rni
                                   // conversion of the column sums, 1 Garner (Eq. garner_mrc),
                                   // 2 direct CRT on the integer pipe only

@@ -442,7 +442,10 @@ static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t
                           size_t dp, size_t db, int npoly, int nbatch, int r, int sbits, const int32_t* item_bits,
                           cudaStream_t st) {
   const int N = ctx->N;
-  if (!ctx->d_lift_tc || (ctx->crt_mode != FHE_CRT_DIRECT && ctx->crt_mode != FHE_CRT_DIRECT_CVT) || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
+  const bool want_tc = ctx->lift_form == FHE_LIFT_TC ||
+                       (ctx->lift_form == FHE_LIFT_AUTO &&
+                        (ctx->crt_mode == FHE_CRT_DIRECT || ctx->crt_mode == FHE_CRT_DIRECT_CVT));
+  if (!ctx->d_lift_tc || !want_tc || L >= 64 || r > 128 || N % kLtRows != 0) return 0;
   LtShape sh;
   sh.r = r;
   sh.L = L;

@@ -655,7 +655,7 @@ static void cols_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows,
 
 int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
-  if (logN <= 12 || (size_t)nbatch * 4 * r > 65535u) {
+  if (logN <= 12 || (size_t)nbatch * 4 * r > 65535u || ctx->ntt_form == FHE_NTT_SPLIT) {
     int rc = launch_ntt(ctx, X, nbatch * 4, r, r, r, false, st);
     if (!rc) rc = launch_pointwise_tensor(ctx, X, r, nbatch, st);
     return rc ? rc : launch_ntt(ctx, X, nbatch, 3 * r, 4 * r, r, true, st);
@@ -681,7 +681,7 @@ int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krow
                     cudaStream_t st) {
   const int logN = ctx->prm.logN, N = ctx->N;
   if (r > krows) return FHE_EINVAL;
-  if (logN <= 12 || (size_t)nbatch * 2 * r > 65535u) {
+  if (logN <= 12 || (size_t)nbatch * 2 * r > 65535u || ctx->ntt_form == FHE_NTT_SPLIT) {
     int rc = launch_ntt(ctx, Y, nbatch, r, 2 * r, r, false, st);
     if (!rc) rc = launch_pointwise_key(ctx, Y, K, krows, r, nbatch, st);
     return rc ? rc : launch_ntt(ctx, Y, nbatch * 2, r, r, r, true, st);
@@ -710,7 +710,7 @@ int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const u
     set_error("key_perm: bad arguments (r %d, key rows %d, g %u)", r, krows, g);
     return FHE_EINVAL;
   }
-  if (logN <= 12 || (size_t)nbatch * r > 65535u) {
+  if (logN <= 12 || (size_t)nbatch * r > 65535u || ctx->ntt_form == FHE_NTT_SPLIT) {
     if ((size_t)nbatch * r > 65535u) {
       set_error("key_perm: %d x %d rows exceed one launch", nbatch, r);
       return FHE_EINVAL;

@@ -78,7 +78,7 @@ class Task:
     """One primitive of a request stage: a multiplication or a rotation."""
 
     req: Request
-    kind: str               # "mult" | "rotate"
+    kind: str               # "mult" | "rotate" | "whole" (the request run alone)
     name: str               # register written
     x: object = None        # operand tensors (2, L, N) views
     y: object = None
@@ -233,6 +233,31 @@ class Server:
             ev.record(st)
         self.busy[si] = (ev, tasks, outs)
 
+    def _solo(self, ready: list):
+        """The request to run whole when the ready work is one request at its first stage and every
+        stream is idle (at low load nothing would join its batches), else None."""
+        if any(b is not None for b in self.busy):
+            return None
+        req = ready[0].req
+        if req.stage != 0 or any(t.req is not req for t in ready):
+            return None
+        return req
+
+    def _launch_whole(self, si: int, req: Request):
+        """All of the request's work as plain calls on stream si (the per-op path), one event at the end."""
+        torch = self.torch
+        st = self.streams[si]
+        st.wait_stream(torch.cuda.current_stream())
+        self._pending_ready_drop(req)
+        with torch.cuda.stream(st):
+            out = per_op_request(self.ctx, self.pool, req, self.k)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        self.busy[si] = (ev, [Task(req, "whole", "out")], [out])
+
+    def _pending_ready_drop(self, req: Request):
+        self._ready_ref[:] = [t for t in self._ready_ref if t.req is not req]
+
     def _pick_batch(self, ready: list) -> list:
         """Tasks of one kind from the oldest ready request: mults of any level, rotations of one (step, level)."""
         if not ready:
@@ -255,6 +280,7 @@ class Server:
         arrivals = deque(sorted(requests, key=lambda r: r.t_arrive))
         queue = deque()
         ready = []
+        self._ready_ref = ready
         waiting = {}   # request id -> number of outstanding tasks
         finishing = deque()  # (event, request): final limb work in flight
         failed_ids = set()
@@ -306,6 +332,18 @@ class Server:
                     self.busy[si] = None
                     progressed = True
                     bad = self.fail_batch is not None and self.fail_batch(si, b[1])
+                    if b[1] and b[1][0].kind == "whole":  # a request that ran whole on this stream
+                        req = b[1][0].req
+                        if bad:
+                            req.error = f"stream {si} reported an error"
+                            failed_ids.add(req.rid)
+                            in_use -= req.footprint
+                            failed.append(req)
+                        else:
+                            req.result = b[2][0]
+                            req.result.record_stream(torch.cuda.current_stream())
+                            complete(req, (time.perf_counter() - t0) / time_scale)
+                        continue
                     for t, o in zip(b[1], b[2]):
                         req = t.req
                         if req.rid in failed_ids:
@@ -334,12 +372,20 @@ class Server:
                 ready[:] = [t for t in ready if t.req.rid not in failed_ids]
             for si in range(len(self.streams)):
                 if self.busy[si] is None and ready:
+                    solo = self._solo(ready)
+                    if solo is not None:  # nothing to batch with: run the whole request on this stream
+                        self._launch_whole(si, solo)
+                        progressed = True
+                        continue
                     batch = self._pick_batch(ready)
                     if batch:
                         self._launch(si, batch)
                         progressed = True
             if not progressed:
-                time.sleep(0.0002)
+                in_flight = finishing or any(b is not None for b in self.busy)
+                if not in_flight:  # idle: sleep until the next arrival (at most 1 ms)
+                    nxt = arrivals[0].t_arrive * time_scale if arrivals else now * time_scale + 0.001
+                    time.sleep(min(max(nxt - (time.perf_counter() - t0), 0.0), 0.001))
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t0) / time_scale
         return _stats(done, len(requests), wall, failed=len(failed), callback_errors=cb_errors)

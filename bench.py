@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--workload", default="ns", choices=["ns", "batched", "serving", "rotations"],
                     help="ns: the headline N=2^16 logQ=1200 batch; batched: 512 uneven pairs, graph vs per-op")
+    ap.add_argument("--ntt", default="fused", choices=["fused", "groups", "split"],
+                    help="transform schedule of the ring products (fhe_set_forms)")
     ap.add_argument("--crt", default="direct", choices=["direct", "garner", "int"],
                     help="RNS->limb reconstruction: exact CRT with rounded quotient (dense sum on the tensor "
                          "cores), Garner mixed radix, or the exact CRT on the integer pipe only")
@@ -314,6 +316,8 @@ def run_ours(args):
     g = fs.rng(77 + rank)
     crt = {"garner": fhe.FHE_CRT_GARNER, "int": fhe.FHE_CRT_DIRECT_INT, "direct": fhe.FHE_CRT_DIRECT}[args.crt]
     ctx = fhe.Context(LOGN, LOGQ, LOGP, crt=crt)
+    ntt_form = {"fused": fhe.FHE_NTT_FUSED, "groups": fhe.FHE_NTT_FUSED_GROUPS, "split": fhe.FHE_NTT_SPLIT}[args.ntt]
+    fhe.fhe_set_forms(ctx, crt, fhe.FHE_LIFT_AUTO, ntt_form)
     ctx.keygen_inject(fs.ternary(g, (), N), fs.uniform_limbs(g, (), N, LOGQ), fs.gaussian(g, (), N),
                fs.uniform_limbs(g, (), N, LOGQ + LOGP), fs.gaussian(g, (), N))
 
@@ -472,7 +476,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "ct/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded encryptions of encoded-size plaintexts)",
-        "config": {"workload": WORKLOAD, "cnum": cnum, "logN": LOGN, "logQ": LOGQ, "logP": LOGP, "crt": args.crt,
+        "config": {"workload": WORKLOAD, "cnum": cnum, "logN": LOGN, "logQ": LOGQ, "logP": LOGP, "crt": args.crt, "ntt": args.ntt,
                    "log_scale": K_RESCALE, "primes": work["primes"],
                    "l2": f"inputs larger than L2: {2 * A.data.numel() * 4 / 1e9:.2f} GB of ciphertexts per step"},
         "latency": {"cnum": 1, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
@@ -527,9 +531,11 @@ def run_batched(args):
             fs.uniform_limbs(g, (1, 2), N, logQ).view(np.int32).copy()).cuda(), logQ)
         items.append(batch.Item(logN, logQ, mk(), mk()))
     runner = batch.BatchRunner(ctxs, K_RESCALE)
-    tuned = batch.Autotuner().tune(runner, items, reps=1)
+    tuner = batch.Autotuner()
+    tuned = tuner.tune(runner, items, reps=1)
     plan = runner.plan(items, tuned["schedule"])
     runner.pack(plan, items)
+    form_ms = tuner.tune_forms(runner, plan, reps=2)
     runner.capture(plan)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -549,8 +555,16 @@ def run_batched(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_per_op = e0.elapsed_time(e1) / args.steps
+    runner.per_level(items)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        lev = runner.per_level(items)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_level = e0.elapsed_time(e1) / args.steps
     got = runner.outputs(plan, items)
-    identical = all(torch.equal(got[i], ref[i].data[0]) for i in range(len(items)))
+    identical = all(torch.equal(got[i], ref[i].data[0]) and torch.equal(got[i], lev[i]) for i in range(len(items)))
     launches_graph = sum(16 for _ in plan.groups)
     line = {
         "metric": "uneven-batch HMult+relin+rescale pairs/s (N 2^13..2^16, logQ 200..1200)",
@@ -561,7 +575,12 @@ def run_batched(args):
                                "scale 2^40, one CUDA-graph launch", "items": len(items),
                    "schedule": {str(k): v for k, v in tuned["schedule"].items()}, "groups": len(plan.groups)},
         "per_op": {"value": len(items) / (ms_per_op / 1e3), "ms_per_step": ms_per_op, "launches": 15 * len(items)},
-        "speedup_vs_per_op": ms_per_op / ms_graph, "identical_results": bool(identical),
+        "per_level": {"value": len(items) / (ms_per_level / 1e3), "ms_per_step": ms_per_level,
+                      "how": "one fhe_mult_relin_rescale per (ring, exact level), pairs of a level stacked"},
+        "speedup_vs_per_op": ms_per_op / ms_graph, "speedup_vs_per_level": ms_per_level / ms_graph,
+        "identical_results": bool(identical),
+        "group_forms": [[g.logN, g.L_pad, len(g.idx), list(g.forms)] for g in plan.groups],
+        "form_timings_ms": form_ms,
         "graph_kernels_approx": launches_graph,
         "autotune_ms": {str(k): v for k, v in tuned["timings_ms"].items()},
     }

@@ -393,6 +393,9 @@ int fhe_mult_relin_rescale_noalloc(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* 
 #define FHE_NTT_FUSED 0  /* N > 2^12: column pass, one fused row pass (forward rows, products,
                             inverse rows), column pass                                        */
 #define FHE_NTT_SPLIT 1  /* full forward transforms, pointwise products, full inverse transforms */
+#define FHE_NTT_FUSED_GROUPS 2 /* the fused row pass of the tensor product with one operand row per
+                                  16-thread group (smaller per-thread code), products through
+                                  shared memory                                                 */
 int fhe_set_forms(fhe_ctx* ctx, int crt, int lift, int ntt);
 
 /* Diagnostics (no counterpart in the paper; measurement support).

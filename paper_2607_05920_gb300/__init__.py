@@ -53,6 +53,7 @@ FHE_LIFT_INT = 1
 FHE_LIFT_TC = 2
 FHE_NTT_FUSED = 0
 FHE_NTT_SPLIT = 1
+FHE_NTT_FUSED_GROUPS = 2
 FHE_SAMPLE_UNIFORM = 0
 FHE_SAMPLE_TERNARY = 1
 FHE_SAMPLE_HWT = 2

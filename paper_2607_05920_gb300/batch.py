@@ -10,8 +10,12 @@ the whole batch is one graph launch from the host.
 
 The level buckets are the prime-count schedule: a wider bucket pads more
 ciphertexts to more NTT primes and limbs, a narrower one costs more launches.
-`Autotuner` measures candidate schedules on the batch at hand and keeps the
-fastest per (GPU, ring size, batch size class).
+`Autotuner` searches two levels of schedule on the batch at hand: the bucket
+count per ring size, then for every group the kernel forms of its ring
+products (tensor-core or integer reconstruction, tensor-core or integer lift,
+fused or split transform schedule; `fhe_set_forms`), and keeps the fastest,
+cached per (GPU, ring size, limb count, batch size class).  Every form gives
+bit-identical results, so the choice is a pure schedule.
 
 All arithmetic runs in the library's kernels; this module only plans, packs
 (device-to-device copies into padded tensors) and launches.
@@ -24,7 +28,14 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (FHE_OP_MULT, Ciphertext, Context, fhe_mult_relin_rescale, fhe_mult_relin_rescale_ragged, limbs)
+from . import (FHE_CRT_DIRECT, FHE_CRT_DIRECT_INT, FHE_LIFT_AUTO, FHE_LIFT_INT, FHE_LIFT_TC, FHE_NTT_FUSED,
+               FHE_NTT_FUSED_GROUPS, FHE_NTT_SPLIT, Ciphertext, Context, fhe_mult_relin_rescale,
+               fhe_mult_relin_rescale_ragged, fhe_set_forms, limbs)
+
+# (reconstruction, lift, transform schedule) candidates of a group
+FORMS = tuple((c, l, t) for c in (FHE_CRT_DIRECT, FHE_CRT_DIRECT_INT) for l in (FHE_LIFT_TC, FHE_LIFT_INT)
+              for t in (FHE_NTT_FUSED, FHE_NTT_FUSED_GROUPS, FHE_NTT_SPLIT))
+DEFAULT_FORMS = (FHE_CRT_DIRECT, FHE_LIFT_AUTO, FHE_NTT_FUSED)
 
 
 @dataclass
@@ -48,6 +59,7 @@ class Group:
     B: object = None
     O: object = None
     bits: object = None
+    forms: tuple = DEFAULT_FORMS
 
 
 def bucket_bounds(levels: list[int], nbuckets: int) -> list[int]:
@@ -114,9 +126,15 @@ class BatchRunner:
                 g.A[j, :, :L].copy_(items[i].a.data[0])
                 g.B[j, :, :L].copy_(items[i].b.data[0])
 
+    def run_group(self, g: Group, forms=None) -> None:
+        fhe_set_forms(g.ctx, *(forms or g.forms))
+        fhe_mult_relin_rescale_ragged(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.k)
+
     def run(self, plan: Plan) -> None:
         for g in plan.groups:
-            fhe_mult_relin_rescale_ragged(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.k)
+            self.run_group(g)
+        for c in {id(g.ctx): g.ctx for g in plan.groups}.values():
+            fhe_set_forms(c, *DEFAULT_FORMS)
 
     def capture(self, plan: Plan):
         """Capture run(plan) into a CUDA graph (workspaces are sized by a first eager run)."""
@@ -141,6 +159,24 @@ class BatchRunner:
             for j, i in enumerate(g.idx):
                 out[i] = g.O[j, :, :limbs(items[i].logQ - self.k)].contiguous()
         return out
+
+    def per_level(self, items: list[Item]) -> list:
+        """CipherTensor calls without raggedness: one fhe_mult_relin_rescale per (ring, exact level) with all
+        pairs of that level stacked (cnum = their count)."""
+        torch = self.torch
+        by = {}
+        for i, it in enumerate(items):
+            by.setdefault((it.logN, it.logQ), []).append(i)
+        res = [None] * len(items)
+        for (logN, logQ), idx in sorted(by.items()):
+            ctx = self.ctx[logN]
+            a = Ciphertext(torch.cat([items[i].a.data for i in idx]), logQ)
+            b = Ciphertext(torch.cat([items[i].b.data for i in idx]), logQ)
+            o = ctx.empty_ct(len(idx), logQ - self.k)
+            fhe_mult_relin_rescale(ctx, a, b, self.k, o)
+            for j, i in enumerate(idx):
+                res[i] = o.data[j]
+        return res
 
     def per_op(self, items: list[Item]) -> list:
         """The plain path: one fhe_mult_relin_rescale call per pair (cnum = 1)."""
@@ -171,6 +207,46 @@ class Autotuner:
     def key(gpu: str, logN: int, n: int) -> str:
         size_class = 1 << max(0, int(np.ceil(np.log2(max(1, n)))))
         return f"{gpu}|N=2^{logN}|n<={size_class}"
+
+    @staticmethod
+    def forms_key(gpu: str, g: Group) -> str:
+        size_class = 1 << max(0, int(np.ceil(np.log2(max(1, len(g.idx))))))
+        return f"{gpu}|N=2^{g.logN}|L={g.L_pad}|n<={size_class}|forms"
+
+    def tune_forms(self, runner: BatchRunner, plan: Plan, reps: int = 2) -> dict:
+        """Per group: time every kernel form, keep the fastest (cached); returns {group index: ms per form}."""
+        torch = runner.torch
+        gpu = torch.cuda.get_device_name()
+        report = {}
+        for gi, g in enumerate(plan.groups):
+            key = self.forms_key(gpu, g)
+            if key in self.cache:
+                g.forms = tuple(self.cache[key])
+                continue
+            timings = {}
+            for f in FORMS:
+                runner.run_group(g, f)  # warm (and sizes the workspace)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    runner.run_group(g, f)
+                e1.record()
+                e1.synchronize()
+                timings[f] = e0.elapsed_time(e1) / reps
+            g.forms = min(timings, key=timings.get)
+            self.cache[key] = list(g.forms)
+            report[gi] = {"/".join(map(str, f)): round(t, 4) for f, t in timings.items()}
+            fhe_set_forms(g.ctx, *DEFAULT_FORMS)
+        self._save()
+        return report
+
+    def _save(self):
+        if self.cache_path:
+            try:
+                json.dump(self.cache, open(self.cache_path, "w"), indent=1)
+            except OSError:
+                pass
 
     def tune(self, runner: BatchRunner, items: list[Item], reps: int = 2) -> dict:
         torch = runner.torch
@@ -207,9 +283,5 @@ class Autotuner:
                 self.cache[key] = nb
                 report[logN] = timings
             schedule[logN] = bucket_bounds(levels, nb)
-        if self.cache_path:
-            try:
-                json.dump(self.cache, open(self.cache_path, "w"), indent=1)
-            except OSError:
-                pass
+        self._save()
         return {"schedule": schedule, "timings_ms": report}

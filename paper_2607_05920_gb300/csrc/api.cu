@@ -404,7 +404,7 @@ int fhe_primes_for_bound(int bound_bits) { return primes_for_bound_global(bound_
 
 int fhe_set_forms(fhe_ctx* ctx, int crt, int lift, int ntt) {
   if (!ctx || crt < FHE_CRT_DIRECT || crt > FHE_CRT_DIRECT_CVT || lift < FHE_LIFT_AUTO || lift > FHE_LIFT_TC ||
-      (ntt != FHE_NTT_FUSED && ntt != FHE_NTT_SPLIT)) {
+      (ntt != FHE_NTT_FUSED && ntt != FHE_NTT_SPLIT && ntt != FHE_NTT_FUSED_GROUPS)) {
     set_error("set_forms: bad arguments (crt %d, lift %d, ntt %d)", crt, lift, ntt);
     return FHE_EINVAL;
   }

@@ -468,6 +468,71 @@ __global__ void __launch_bounds__(16 * kRowsPerCta, 5) k_ntt_rows_tensor(uint32_
     for (int k = 0; k < 16; ++k) base[o * rowN + j0 + 16 * k] = y[o][k];
 }
 
+// The same pass with one operand per 16-thread group: a CTA takes 4 matrix rows of one
+// (ciphertext, prime); group g (0..15) runs the forward row stages of operand g % 4 of row g / 4
+// and leaves the transformed row in shared memory; after a barrier, group g < 12 forms output
+// g % 3 of row g / 3 (D0 = B1 B2, D1 = A1 B2 + A2 B1, D2 = A1 A2, Montgomery) for its 16 positions
+// and runs that output's inverse row stages (warps 6 and 7 sit out).  A thread's code covers one
+// operand instead of four, which keeps the pass's instruction footprint small.
+constexpr int kGRows = 4;  // matrix rows per CTA
+__global__ void __launch_bounds__(256) k_ntt_rows_tensor_g(uint32_t* __restrict__ X, int r, int logN,
+                                                           const uint2* __restrict__ tw,
+                                                           const uint2* __restrict__ itw,
+                                                           const uint32_t* __restrict__ qtab,
+                                                           const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[16 * kSlot];
+  const int grp = threadIdx.x >> 4, j0 = threadIdx.x & 15;
+  const int N = 1 << logN;
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
+  const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
+  const size_t rowN = (size_t)r * N;
+  uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N;
+  {
+    const int row = grp >> 2, op = grp & 3;
+    const int c = blockIdx.x * kGRows + row;
+    const uint32_t* a = base + op * rowN + (size_t)c * kRowLen;
+    uint32_t x[1][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[0][k] = a[j0 + 16 * k];
+    uint32_t* sr = s + grp * kSlot;
+    rows_fwd_multi<1>(x, c, j0, sr, N, tw + (size_t)p * N, q);
+    __syncwarp();  // the exchange reads of this slot are done
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sr[rpad(16 * j0 + j)] = reduce4(x[0][j], q);
+  }
+  __syncthreads();
+  uint32_t y[1][16];
+  int row = 0, o = 0;
+  if (grp < 12) {
+    row = grp / 3;
+    o = grp - 3 * row;
+    const uint32_t* B1 = s + (row * 4 + 0) * kSlot;
+    const uint32_t* A1 = s + (row * 4 + 1) * kSlot;
+    const uint32_t* B2 = s + (row * 4 + 2) * kSlot;
+    const uint32_t* A2 = s + (row * 4 + 3) * kSlot;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int pos = rpad(16 * j0 + j);
+      if (o == 0) {
+        y[0][j] = mont_mul(B1[pos], B2[pos], q, qi);
+      } else if (o == 2) {
+        y[0][j] = mont_mul(A1[pos], A2[pos], q, qi);
+      } else {
+        y[0][j] = add_mod(mont_mul(A1[pos], B2[pos], q, qi), mont_mul(A2[pos], B1[pos], q, qi), q);
+      }
+    }
+  }
+  __syncthreads();  // every product read its operands: the slots are free for the inverse exchanges
+  if (grp < 12) {
+    const int c = blockIdx.x * kGRows + row;
+    rows_inv_multi<1>(y, c, j0, s + grp * kSlot, N, itw + (size_t)p * N, q);
+    uint32_t* d = base + o * rowN + (size_t)c * kRowLen;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) d[j0 + 16 * k] = y[0][k];
+  }
+}
+
 // Key product of a key switch (Sec. 6): Y = [batch][2][r][N] holds the lifted
 // polynomial in block 0 after the forward column stages; the kernel finishes
 // its transform, multiplies it by the key rows K[0][p], K[1][p] (transform
@@ -666,9 +731,14 @@ int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaS
   }
   {
     ProfScope ps(ctx, FHE_K_NTT_PW, 1, st);
-    dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
-    k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi2, ctx->d_ipsi2,
-                                                         ctx->d_q, ctx->d_qinv);
+    if (ctx->ntt_form == FHE_NTT_FUSED_GROUPS) {
+      dim3 grid((N >> 8) / kGRows, nbatch * r);
+      k_ntt_rows_tensor_g<<<grid, 256, 0, st>>>(X, r, logN, ctx->d_psi2, ctx->d_ipsi2, ctx->d_q, ctx->d_qinv);
+    } else {
+      dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
+      k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi2, ctx->d_ipsi2,
+                                                           ctx->d_q, ctx->d_qinv);
+    }
   }
   {
     ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);

@@ -79,3 +79,48 @@ def test_bucket_bounds_cover_and_split():
         b = batch.bucket_bounds(lv, nb)
         assert b[-1] == 1200 and b == sorted(set(b)) and len(b) <= min(nb, len(lv))
     assert batch.bucket_bounds(lv, 1) == [1200]
+
+
+def test_form_search_gives_identical_results_at_the_batched_ring_sizes():
+    """Rings 2^13 and 2^16 (two-pass transforms, tensor-core and integer forms): every kernel form of a group
+    gives the same ciphertexts; the tuned graph equals per-level CipherTensor calls and per-op calls."""
+    import torch
+
+    from paper_2607_05920_gb300 import batch
+
+    pairs = {13: make_pair(13, 1200, 1200, seed=54), 16: make_pair(16, 1200, 1200, seed=55)}
+    ctxs = {k: p.ctx for k, p in pairs.items()}
+    items = _items(pairs, 6, 56, 200, 1200)
+    for logN in (13, 16):  # both rings present, one item near the top level
+        N = 1 << logN
+        from paper_2607_05920_gb300 import Ciphertext
+
+        la = fs.uniform_limbs(fs.rng(logN), (1, 2), N, 1190)
+        lb = fs.uniform_limbs(fs.rng(logN + 1), (1, 2), N, 1190)
+        items.append(batch.Item(logN, 1190, Ciphertext(to_dev(la), 1190), Ciphertext(to_dev(lb), 1190)))
+    runner = batch.BatchRunner(ctxs, 40)
+    plan = runner.plan(items, {13: [1200], 16: [1200]})
+    runner.pack(plan, items)
+    outs = []
+    for f in batch.FORMS:
+        for g in plan.groups:
+            runner.run_group(g, f)
+        torch.cuda.synchronize()
+        outs.append([g.O.clone() for g in plan.groups])
+    for o in outs[1:]:
+        assert all(torch.equal(x, y) for x, y in zip(o, outs[0]))
+    tuner = batch.Autotuner()
+    tuner.tune_forms(runner, plan, reps=1)
+    assert all(g.forms in batch.FORMS for g in plan.groups)
+    runner.capture(plan)
+    for g in plan.groups:
+        g.O.zero_()
+    runner.graph.replay()
+    torch.cuda.synchronize()
+    got = runner.outputs(plan, items)
+    ref, lev = runner.per_op(items), runner.per_level(items)
+    torch.cuda.synchronize()
+    for i in range(len(items)):
+        assert torch.equal(got[i], ref[i].data[0]) and torch.equal(got[i], lev[i]), i
+    for p in pairs.values():
+        p.ctx.close()

@@ -109,8 +109,12 @@ def test_sparse_secret_workload_pair_and_rotations():
     dec = bigint.from_limbs(P.ctx.decrypt(out).cpu().numpy().view(np.uint32)[0], signed=True)
     z = encode.decode(dec, N, 40, n)
     assert np.abs(z - z1 * z2).max() <= 2.0 ** -20 * max(1.0, np.abs(z1 * z2).max())
-    for step in steps:
+    import torch
+
+    hoisted = P.ctx.rotate_hoisted(ca, steps)
+    for step, h in zip(steps, hoisted):
         got = P.ctx.rotate(ca, step)
+        assert torch.equal(h.data, got.data), step
         assert ct_ints(got)[0] == tuple(ckks.rotate(oa[0], step, P.rtk[step], N, 880, 880)), step
         dec = bigint.from_limbs(P.ctx.decrypt(got).cpu().numpy().view(np.uint32)[0], signed=True)
         assert np.abs(encode.decode(dec, N, 40, n) - np.roll(z1, -step)).max() <= 2.0 ** -20, step

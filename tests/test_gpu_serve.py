@@ -103,3 +103,28 @@ def test_injected_failures_fail_only_their_own_requests():
         if not r.error.startswith("stream"):
             assert torch.equal(r.result, by_id[r.rid].result), (r.rid, r.op)
     ctx.close()
+
+
+def test_served_mult_at_the_serving_modulus_matches_oracle():
+    """logQ = logP = 1550 (the serving workload's top level) on a ring of 2^12: served multiplications at two
+    levels, ragged in one batch, equal the oracle's."""
+    import paper_2607_05920_gb300 as fhe
+    from paper_2607_05920_gb300 import serve
+
+    P = make_pair(12, 1550, 1550, seed=65)
+    ctx = P.ctx
+    g = fs.rng(66)
+    levels = [1550, 1540]  # both 49 limbs: one ragged batch
+    pool = {lq: fhe.Ciphertext(to_dev(fs.uniform_limbs(g, (2, 2), ctx.N, lq)), lq) for lq in levels}
+    reqs = [serve.Request(i, 0.0, "mult", levels[i % 2], i % 2, (i + 1) % 2) for i in range(4)]
+    srv = serve.Server(ctx, pool, k=40, budget_bytes=4 << 30, max_batch=8, streams=2)
+    stats = srv.run(reqs)
+    assert stats["completed"] == 4
+    for r in reqs[:2]:
+        ha = pool[r.logQ].data.cpu().numpy().view(np.uint32)
+        oa = tuple(bigint.from_limbs(ha[r.a, p]) for p in range(2))
+        ob = tuple(bigint.from_limbs(ha[r.b, p]) for p in range(2))
+        want = ckks.rescale(ckks.mult(oa, ob, P.evk, r.logQ, 1550), 40, r.logQ)
+        host = r.result.cpu().numpy().view(np.uint32)
+        assert tuple(bigint.from_limbs(host[p]) for p in range(2)) == tuple(want), r.logQ
+    ctx.close()

@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
-    ap.add_argument("--workload", default="ns", choices=["ns", "batched", "serving", "rotations"],
+    ap.add_argument("--workload", default="ns", choices=["ns", "batched", "serving", "rotations", "bgv"],
                     help="ns: the headline N=2^16 logQ=1200 batch; batched: 512 uneven pairs, graph vs per-op")
     ap.add_argument("--ntt", default="fused", choices=["fused", "groups", "split"],
                     help="transform schedule of the ring products (fhe_set_forms)")
@@ -738,6 +738,72 @@ def run_rotations(args):
     ctx.close()
 
 
+def run_bgv(args):
+    """BGV at N=2^14, t=65537, chain Q_l = q0 r^l (q0 ~ 2^54, r ~ 2^48, 8 levels, logQ=438, P = 2^438): a batch of
+    128 ciphertexts squared 8 times with relinearisation and a modulus switch after each; the decryptions are
+    checked against m^(2^8) mod (X^N + 1, t) computed on the GPU by the same scheme's plaintext rule."""
+    import numpy as np
+    import torch
+
+    import paper_2607_05920_gb300 as fhe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t, levels, logN, cnum = 65537, 8, 14, 128
+    # q0, r: the largest odd values = 1 mod t below 2^54 and 2^48 (as the tests choose them)
+    def pick(bits):
+        k = ((1 << bits) - 1) // t
+        if (1 + t * k) % 2 == 0:
+            k -= 1
+        return 1 + t * k
+
+    q0, r = pick(54), pick(48)
+    logQ = (q0 * r ** levels).bit_length()
+    ctx = fhe.Context(logN, logQ, logQ, scheme=fhe.FHE_SCHEME_BGV, t=t, bgv_q0=q0, bgv_r=r, bgv_levels=levels)
+    ctx.keygen(0xB6)
+    N = 1 << logN
+    g = np.random.Generator(np.random.PCG64(303))
+    slots = torch.from_numpy(g.integers(0, t, size=(cnum, N), dtype=np.int64).astype(np.int32)).cuda()
+    ct0 = ctx.encrypt(fhe.fhe_bgv_encode(ctx, slots, logQ), 5)
+
+    def chain():
+        ct = ct0
+        for _ in range(levels):
+            ct = ctx.mod_switch(ctx.mult_relin(ct, ct))
+        return ct
+
+    for _ in range(args.warmup):
+        out = chain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        out = chain()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # slot-wise: x^(2^8) mod t in every slot
+    want = slots.to(torch.int64)
+    for _ in range(levels):
+        want = want * want % t
+    got = fhe.fhe_bgv_decode(ctx, ctx.decrypt(out)).to(torch.int64)
+    line = {
+        "metric": "BGV ciphertexts/s through a depth-8 squaring chain with relinearisation and modulus switching "
+                  "(N=2^14, logQ=438, t=65537)",
+        "value": cnum / (ms / 1e3), "unit": "ct/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "u32",
+        "data": "synthetic (seeded keys and encryptions of slot-encoded uniform plaintexts mod t)",
+        "config": {"workload": "BGV N=2^14, chain q0 r^8 (logQ 438), P=2^438, t=65537, 128 ciphertexts, "
+                               "8 squarings", "cnum": cnum},
+        "homomorphic_mults_per_s": levels * cnum / (ms / 1e3),
+        "decryptions_exact": bool(torch.equal(got, want)), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.workload == "serving" and args.impl != "reference":
@@ -749,6 +815,8 @@ def main():
         run_batched(args)
     elif args.workload == "rotations":
         run_rotations(args)
+    elif args.workload == "bgv":
+        run_bgv(args)
     else:
         run_ours(args)
 

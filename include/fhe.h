@@ -249,7 +249,7 @@ int fhe_decrypt(fhe_ctx* ctx, const fhe_ct* in, uint32_t* pt_out, void* ws, size
  * BGV: same shape modulo the odd Q_l of the operands' level, with the key-switch
  * division (y + delta)/P, delta = t [(-y) t^-1]_P (centred), so delta = 0 mod t.
  * CKKS:
- *   (d0, d1, d2) = (b1 b2, a1 b2 + a2 b1, a1 a2) mod Q    (Karatsuba, Sec. 5)
+ *   (d0, d1, d2) = (b1 b2, a1 b2 + a2 b1, a1 a2) mod Q    (4 forward, 3 inverse NTTs, Sec. 5)
  *   out = (d0, d1) + round(P^-1 (d2~ evk_b, d2~ evk_a) mod P Q)  (mod Q),
  * d2~ the centred representative of d2 (logQ-bit two's complement).
  * a, b: same logQ; b->cnum = a->cnum (pairwise mode) or 1 (broadcast mode: the

@@ -373,7 +373,7 @@ int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* ou
   }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ctw = 2 * (size_t)L * N;  // words per input ciphertext
-  // tensor product: lift (b1, a1) and (b2, a2), 4 forward NTTs, Karatsuba, 3 INTTs, Garner
+  // tensor product: lift (b1, a1) and (b2, a2), 4 forward NTTs, 3 products, 3 INTTs, reconstruction
   const size_t btw = b->cnum == 1 ? 0 : ctw;  // broadcast mode: every item reads the one b
   RET_IF(launch_lift(ctx, a->data, L, (size_t)L * N, ctw, X, (size_t)rt * N, 4 * (size_t)rt * N, 2, cnum, rt, st));
   RET_IF(launch_lift(ctx, b->data, L, (size_t)L * N, btw, X + 2 * (size_t)rt * N, (size_t)rt * N,

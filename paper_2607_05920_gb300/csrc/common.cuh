@@ -230,6 +230,15 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t q,
   return (hi < mh) ? r + q : r;
 }
 
+// The same product left in (0, 2q): hi - mh + q.  Needs a b < q 2^32 (one operand may be in
+// [0, 4q) when the other is in [0, q)).
+__device__ __forceinline__ uint32_t mont_mul_lazy(uint32_t a, uint32_t b, uint32_t q, uint32_t qinv) {
+  const uint32_t lo = a * b;
+  const uint32_t hi = __umulhi(a, b);
+  const uint32_t mh = __umulhi(lo * qinv, q);
+  return hi - mh + q;
+}
+
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t q) {
   uint32_t s = a + b;  // a, b < q < 2^30: no overflow
   return s >= q ? s - q : s;

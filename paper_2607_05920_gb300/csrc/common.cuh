@@ -101,7 +101,8 @@ struct fhe_ctx {
   uint2* d_psi2 = nullptr;        // [R][N] (psi^brv(k), floor(w 2^32 / q)): forward twiddles (bit-reversed
                                   // order) with their Shoup companions, one 64-bit load per butterfly
   uint2* d_ipsi2 = nullptr;       // [R][N] (psi^-brv(k), Shoup companion)
-  uint32_t* d_nscale = nullptr;   // [R]  N^-1 * 2^32 mod q (INTT scale, undoes one Montgomery factor)
+  uint32_t* d_nscale = nullptr;   // [R]  N^-1 * 2^32 mod q (INTT scale, undoes one Montgomery factor;
+                                  // applied in the reconstruction)
   uint32_t* d_nscale_sh = nullptr;// [R]
   uint32_t* d_pow2 = nullptr;     // [R][kMaxLiftLimbs] 2^(32 l) mod q
   uint32_t* d_pow24 = nullptr;    // [R][kLiftDigits] 2^(24 m) mod q
@@ -110,7 +111,7 @@ struct fhe_ctx {
   uint32_t* d_mprod = nullptr;    // [R+1][kMaxLimbs] prod_{i<k} q_i mod 2^(32 kMaxLimbs)
   // direct CRT over the first r primes, for every r in [1, R]; rows of set r start at r(r-1)/2
   uint32_t* d_crt_qhat = nullptr; // [R(R+1)/2][kMaxLimbs] (M_r / q_i) mod 2^(32 kMaxLimbs)
-  uint2* d_crt_inv = nullptr;     // [R(R+1)/2] {[(M_r / q_i)^-1]_{q_i}, shoup}
+  uint2* d_crt_inv = nullptr;     // [R(R+1)/2] {[(M_r / q_i)^-1 N^-1 2^32]_{q_i}, shoup}
   uint32_t* d_crt_negm = nullptr; // [R+1][kMaxLimbs] (-M_r) mod 2^(32 kMaxLimbs)
   float* d_invq = nullptr;        // [R] 1/q_i rounded to fp32
   uint32_t* d_crt_dig = nullptr;  // per r: [r+1][kCrtDigits] 24-bit digits of (M_r/q_i) mod 2^4096, last row -M_r
@@ -266,8 +267,10 @@ int launch_lift_small(const fhe_ctx* ctx, const void* src, bool is_i8, size_t sr
                       size_t dst_bstride, int nbatch, int r, cudaStream_t st);
 
 // In-place negacyclic NTT / INTT on `rows` rows of N words; row k uses prime
-// (k % r) -- rows are grouped [..][r][N].  The inverse includes the scale
-// N^-1 2^32 (one Montgomery factor is undone).
+// (k % r) -- rows are grouped [..][r][N].  The inverse leaves its result in
+// [0, 2q) without the scale N^-1 2^32 (which also undoes one Montgomery
+// factor): the reconstruction's constants (d_crt_inv) and Garner's first step
+// apply it, so an inverse transform must be followed by launch_garner.
 //  rows are taken in `ngroups` groups of `group_rows` consecutive rows, group g
 //  starting at row g * group_stride; within a group, row k uses prime k % r.
 int launch_ntt(const fhe_ctx* ctx, uint32_t* data, int ngroups, int group_rows, int group_stride, int r,

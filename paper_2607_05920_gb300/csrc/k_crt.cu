@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
                                                         size_t out_bstride, EpiArgs epi, int N,
                                                         const uint32_t* __restrict__ qtab,
                                                         const uint2* __restrict__ gtab, int R,
-                                                        const uint32_t* __restrict__ mprod) {
+                                                        const uint32_t* __restrict__ mprod,
+                                                        const uint32_t* __restrict__ nscale,
+                                                        const uint32_t* __restrict__ nscale_sh) {
   extern __shared__ uint32_t sv[];  // [rows][kCrtThreads], one column per thread
   const int tid = threadIdx.x;
   constexpr int cstride = kCrtThreads;
@@ -168,8 +170,9 @@ __global__ void __launch_bounds__(kCrtThreads) k_garner(const uint32_t* __restri
 
   // 1. mixed-radix digits
   for (int k = 0; k < r; ++k) {
-    uint32_t x = __ldg(src + (size_t)k * N);
     const uint32_t qk = __ldg(qtab + k), twoq = 2u * qk;
+    // the inverse transform's N^-1 2^32 scale, left out there
+    uint32_t x = shoup_mul(__ldg(src + (size_t)k * N), __ldg(nscale + k), __ldg(nscale_sh + k), qk);
     const uint2* crow = gtab + (size_t)k * R;
     int j = 0;
     for (; j + 4 <= k; j += 4) {
@@ -1251,7 +1254,7 @@ static int garner_launch(const fhe_ctx* ctx, const uint32_t* in, size_t ip, size
   dim3 grid((N + threads - 1) / threads, npoly * nbatch);
   ProfScope ps(ctx, FHE_K_CRT, 1, st);
   k_garner<LB><<<grid, threads, smem, st>>>(in, ip, ib, r, npoly, out, op, ob, epi, N, ctx->d_q, ctx->d_garner,
-                                             ctx->R, ctx->d_mprod);
+                                             ctx->R, ctx->d_mprod, ctx->d_nscale, ctx->d_nscale_sh);
   return FHE_OK;
 }
 

@@ -1,9 +1,9 @@
 // Transform-domain pointwise products and the limb-domain kernels.
 //
 // Pointwise (Sec. 5 "element-wise arithmetic in the NTT domain"): Montgomery
-// products a b 2^-32 (Montgomery 1985); the 2^-32 is undone by the INTT
-// scale N^-1 2^32, so every transform-domain product below is exactly one
-// Montgomery product deep.  The tensor product uses Karatsuba (Sec. 5
+// products a b 2^-32 (Montgomery 1985); the 2^-32 is undone by the inverse
+// transform's scale N^-1 2^32 (applied in the reconstruction), so every
+// transform-domain product below is exactly one Montgomery product deep.  The tensor product uses Karatsuba (Sec. 5
 // "Karatsuba Polynomial Multiplication") on the transformed operands:
 // D0 = B1 B2, D2 = A1 A2, D1 = (A1 + B1)(A2 + B2) - D0 - D2.
 //

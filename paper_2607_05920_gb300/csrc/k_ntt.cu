@@ -4,7 +4,10 @@
 // The psi^j twist of Sec. 5 is merged into the twiddles: the forward transform
 // is the Cooley-Tukey network with the bit-reversed table psi^brv(k) (natural
 // input, bit-reversed output); the inverse is the Gentleman-Sande network with
-// psi^-brv(k) (bit-reversed input, natural output) followed by the N^-1 scale.
+// psi^-brv(k) (bit-reversed input, natural output).  The inverse leaves out the
+// N^-1 scale (and the 2^32 that undoes the Montgomery products' 2^-32) and its
+// final reduction: every inverse transform feeds a reconstruction whose first
+// step multiplies each residue by a per-prime constant, which absorbs both.
 // The bit-reversed order never leaves the device: pointwise products see both
 // operands in the same order.
 //
@@ -65,9 +68,7 @@ struct RowMap {
 template <bool INV>
 __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
                                                    const uint2* __restrict__ tw,
-                                                   const uint32_t* __restrict__ qtab,
-                                                   const uint32_t* __restrict__ nscale,
-                                                   const uint32_t* __restrict__ nscale_sh) {
+                                                   const uint32_t* __restrict__ qtab) {
   extern __shared__ uint32_t s[];
   const int N = 1 << logN;
   const int p = rm.prime_of(blockIdx.x, r);
@@ -98,8 +99,8 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
       }
       __syncthreads();
     }
-    const uint32_t sc = __ldg(nscale + p), scp = __ldg(nscale_sh + p);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = shoup_mul(s[j], sc, scp, q);
+    // left in [0, 2q) and unscaled: the reconstruction folds N^-1 2^32 into its first product
+    for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = s[j];
   }
 }
 
@@ -164,9 +165,7 @@ __global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_fwd(uint
 template <int LOGN1>
 __global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
                                                              const uint2* __restrict__ tw,
-                                                             const uint32_t* __restrict__ qtab,
-                                                             const uint32_t* __restrict__ nscale,
-                                                             const uint32_t* __restrict__ nscale_sh) {
+                                                             const uint32_t* __restrict__ qtab) {
   constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
   __shared__ uint32_t s[N1 * 32];
   const int col = threadIdx.x & 31, j0 = threadIdx.x >> 5;
@@ -204,9 +203,9 @@ __global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint
       gs_bfly(x[k], x[k + h], t2.x, t2.y, q);
     }
   }
-  const uint32_t sc = __ldg(nscale + p), scp = __ldg(nscale_sh + p);
+  // left in [0, 2q) and unscaled: the reconstruction folds N^-1 2^32 into its first product
 #pragma unroll
-  for (int k = 0; k < 16; ++k) a[(size_t)(j0 + TPC * k) * kRowLen] = shoup_mul(x[k], sc, scp, q);
+  for (int k = 0; k < 16; ++k) a[(size_t)(j0 + TPC * k) * kRowLen] = x[k];
 }
 
 // --------------------------------------------------------------- row pass
@@ -679,11 +678,9 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
     const int threads = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
     const size_t smem = (size_t)N * 4;
     if (inverse)
-      k_ntt_small<true><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,
-                                                      ctx->d_nscale_sh);
+      k_ntt_small<true><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q);
     else
-      k_ntt_small<false><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,
-                                                       ctx->d_nscale_sh);
+      k_ntt_small<false><<<rows, threads, smem, st>>>(data, rm, r, logN, tw, ctx->d_q);
     return FHE_OK;
   }
   const int logN1 = logN - 8, N1 = 1 << logN1;
@@ -691,8 +688,7 @@ static int ntt_chunk(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows, in
 #define FHE_NTT_COLS(L)                                                                                    \
   case L:                                                                                                  \
     if (inverse)                                                                                           \
-      k_ntt_cols_inv<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, ctx->d_q, ctx->d_nscale,     \
-                                                  ctx->d_nscale_sh);                                       \
+      k_ntt_cols_inv<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, ctx->d_q);                                       \
     else                                                                                                   \
       k_ntt_cols_fwd<L><<<gcols, 2 << L, 0, st>>>(data, rm, r, logN, tw, ctx->d_q);                   \
     break;
@@ -714,8 +710,7 @@ static void cols_launch(const fhe_ctx* ctx, uint32_t* data, RowMap rm, int rows,
 #define FHE_NTT_COLS_ONLY(L)                                                                                 \
   case L:                                                                                                    \
     if (inverse)                                                                                             \
-      k_ntt_cols_inv<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_ipsi2, ctx->d_q,      \
-                                              ctx->d_nscale, ctx->d_nscale_sh);                              \
+      k_ntt_cols_inv<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_ipsi2, ctx->d_q);                              \
     else                                                                                                     \
       k_ntt_cols_fwd<L><<<g, 2 << L, 0, st>>>(data, rm, r, logN, ctx->d_psi2, ctx->d_q);       \
     break;

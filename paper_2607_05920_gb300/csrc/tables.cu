@@ -422,7 +422,8 @@ int build_tables(fhe_ctx* ctx) {
       const size_t off = (size_t)r * (r - 1) / 2;
       for (int i = 0; i < r; ++i) {
         memcpy(&qhat[(off + i) * kMaxLimbs], &cur[(size_t)i * kMaxLimbs], kMaxLimbs * 4);
-        const uint32_t inv = inv_mod((uint32_t)pm[i], q[i]);
+        // the inverse transforms leave out their N^-1 2^32 scale (see k_ntt.cu): it is folded in here
+        const uint32_t inv = (uint32_t)mulmod64(inv_mod((uint32_t)pm[i], q[i]), nscale[i], q[i]);
         crt_inv[off + i] = make_uint2(inv, shoup_of(inv, q[i]));
       }
       uint64_t c = 1;  // -M_r = ~M_r + 1

@@ -249,7 +249,8 @@ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) 
 }
 
 // ------------------------------------------------------------ launchers
-// Lift: residues of unsigned L-limb integers modulo primes [0, r).
+// Lift: residues of unsigned L-limb integers modulo primes [0, r), as representatives below 2 q
+// (the tensor-core form leaves them in [0, q + 2^17); they feed forward transforms).
 //   src: [npoly][L][N] (poly stride src_stride words), dst: [npoly][r][N]
 //   (poly stride dst_stride words); polys of batch c at src + c*src_bstride.
 int launch_lift(const fhe_ctx* ctx, const uint32_t* src, int L, size_t src_pstride, size_t src_bstride,

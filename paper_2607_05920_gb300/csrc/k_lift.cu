@@ -203,7 +203,9 @@ __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint
 // digits of the 128 coefficients of a tile ([128][K = 4L]) and B the
 // constants ([4r][K]); |S| <= 4L 2^14 < 2^22 for L < 64, exact in fp32 and
 // converted to integers by the 1.5 2^23 magic-number addition.  Adding the
-// folded offset (and 2^17 q_i) and one Montgomery reduction gives x mod q_i.
+// folded offset (and 2^17 q_i) and one Montgomery reduction gives x mod q_i,
+// written as a representative below 2q (the forward transform that follows
+// every lift takes inputs below 4q).
 // The constants stay resident in shared memory for the whole (persistent)
 // kernel; the output columns are split into two TMEM accumulators (residue
 // halves) so each half's drain overlaps the other half's MMAs.  Warp roles:
@@ -414,11 +416,10 @@ __global__ void __launch_bounds__(kLtThreads, 1)
             const uint4 k = PC[i];
             const uint64_t u = (uint64_t)((long long)lo + ((long long)hi << 16)) +
                                (((uint64_t)k.w << 32) | k.z);  // >= 0, < 2^49
-            // Montgomery: (u - m q) / 2^32 with m = u q^-1 mod 2^32, in (-q, 2^17)
+            // Montgomery: (u - m q) / 2^32 with m = u q^-1 mod 2^32, in (-q, 2^17); left as that plus
+            // q, in (0, q + 2^17), below 2q: the forward transform that every lift feeds accepts it
             const uint32_t m = (uint32_t)u * k.y;
-            int32_t res = (int32_t)((uint32_t)(u >> 32) - __umulhi(m, k.x));
-            if (res < 0) res += (int32_t)k.x;
-            d[(size_t)i * N] = (uint32_t)res;
+            d[(size_t)i * N] = (uint32_t)(u >> 32) - __umulhi(m, k.x) + k.x;
           }
         }
       }

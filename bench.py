@@ -273,19 +273,33 @@ def measured_peaks() -> dict:
         return {}
 
 
-def read_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+# the source files that define each kernel class (its own .cu and the headers it includes)
+KERNEL_SOURCES = {
+    "ntt_pw": ("common.cuh", "k_ntt.cu"),
+    "ntt_fwd": ("common.cuh", "k_ntt.cu"),
+    "ntt_inv": ("common.cuh", "k_ntt.cu"),
+    "crt": ("common.cuh", "k_crt.cu", "tc.cuh"),
+    "lift": ("common.cuh", "k_lift.cu", "tc.cuh"),
+}
+
+
+def source_digest(kernel: str) -> str:
+    """sha256 of the kernel class's source files in the listed order, first 16 hex digits."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
-        return None
     src = os.path.join(ROOT, "paper_2607_05920_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    digest = h.hexdigest()[:16]
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
+        return None
+    digest = source_digest(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:

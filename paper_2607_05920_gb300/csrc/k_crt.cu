@@ -505,49 +505,68 @@ __device__ __forceinline__ void relin_setup(RelinStream& rs, const EpiArgs& epi,
 
 // The relinearisation epilogue over a limb column held in shared memory
 // (col[l kTcRows] for l in [min(rl, sl), nx), the exact product X after its
-// carries): the same result as RelinStream, in passes whose loads do not wait
-// on a carry.  In place: the z limbs overwrite the x limbs they replace.
+// carries), in one pass: the shifted and rounded limbs plus the addend (z)
+// and, when k2 > 0, the rescaled and rounded limbs (w) advance together, each
+// new z limb completing the w limb below it, so every column limb is read
+// once and no z limb goes back to shared memory.  Loads come eight at a time
+// ahead of the carry chains.
 //   z_j = ((X + 2^(s-1)) >> s) limb j + addend limb j, mod 2^ob;
 //   out = (Z + 2^(k2-1)) >> k2 mod 2^(ob-k2) (or Z when k2 = 0), zero-padded.
-__device__ __forceinline__ void relin_column(uint32_t* col, int nx, const EpiArgs& epi, int ob, const uint32_t* add,
-                                             int add_stride, uint32_t* dst, int N) {
+__device__ __forceinline__ void relin_column(const uint32_t* col, int nx, const EpiArgs& epi, int ob,
+                                             const uint32_t* add, int add_stride, uint32_t* dst, int N) {
   const int s = epi.shift, sl = s >> 5, sb = s & 31, rl = (s - 1) >> 5, rbit = (s - 1) & 31;
   const int nz = (ob + 31) >> 5;
   const uint32_t zmask = limb_mask(nz - 1, ob);
   const int na = add ? epi.add_limbs : 0;
-  uint32_t cA = (col[(size_t)rl * kTcRows] >> rbit) & 1u, cB = 0u;
-#pragma unroll 4
-  for (int j = 0; j < nz; ++j) {
-    const uint32_t x0 = sl + j < nx ? col[(size_t)(sl + j) * kTcRows] : 0u;
-    const uint32_t x1 = sl + j + 1 < nx ? col[(size_t)(sl + j + 1) * kTcRows] : 0u;
-    const uint32_t a = j < na ? add[(size_t)j * add_stride] : 0u;
-    const uint32_t y = __funnelshift_r(x0, x1, sb) + cA;
-    cA = y < cA ? 1u : 0u;
-    const uint64_t zz = (uint64_t)y + a + cB;
-    cB = (uint32_t)(zz >> 32);
-    uint32_t z = (uint32_t)zz;
-    if (j == nz - 1) z &= zmask;
-    col[(size_t)(sl + j) * kTcRows] = z;
-  }
   const int out_limbs = epi.out_limbs;
-  if (epi.k2 == 0) {
-    for (int i = 0; i < out_limbs; ++i) dst[(size_t)i * N] = i < nz ? col[(size_t)(sl + i) * kTcRows] : 0u;
-    return;
-  }
-  const int k2 = epi.k2, kl = k2 >> 5, kb = k2 & 31, rl2 = (k2 - 1) >> 5, rbit2 = (k2 - 1) & 31;
-  const int fb = ob - k2, nf = (fb + 31) >> 5;
+  const int k2 = epi.k2, kl = k2 >> 5, kb = k2 & 31;
+  const int rl2 = k2 > 0 ? (k2 - 1) >> 5 : -1, rbit2 = (k2 - 1) & 31;
+  const int fb = ob - k2, nf = k2 > 0 ? (fb + 31) >> 5 : nz;
   const uint32_t wmask = limb_mask(nf - 1, fb);
-  uint32_t cC = rl2 < nz ? (col[(size_t)(sl + rl2) * kTcRows] >> rbit2) & 1u : 0u;
-#pragma unroll 4
-  for (int i = 0; i < nf; ++i) {
-    const uint32_t z0 = kl + i < nz ? col[(size_t)(sl + kl + i) * kTcRows] : 0u;
-    const uint32_t z1 = kl + i + 1 < nz ? col[(size_t)(sl + kl + i + 1) * kTcRows] : 0u;
-    uint32_t w = __funnelshift_r(z0, z1, kb) + cC;
+  const int wfirst = k2 > 0 ? kl + 1 : 0;  // z limb that completes w limb 0
+  uint32_t cA = (col[(size_t)rl * kTcRows] >> rbit) & 1u, cB = 0u, cC = 0u;
+  uint32_t xprev = sl < nx ? col[(size_t)sl * kTcRows] : 0u, zprev = 0u;
+  int i = 0;  // next output limb
+  for (int j0 = 0; j0 < nz; j0 += 8) {
+    uint32_t xv[8], av[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = j0 + q;
+      xv[q] = sl + j + 1 < nx ? col[(size_t)(sl + j + 1) * kTcRows] : 0u;
+      av[q] = j < na ? add[(size_t)j * add_stride] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = j0 + q;
+      if (j >= nz) break;
+      const uint32_t y = __funnelshift_r(xprev, xv[q], sb) + cA;
+      cA = y < cA ? 1u : 0u;
+      const uint64_t zz = (uint64_t)y + av[q] + cB;
+      cB = (uint32_t)(zz >> 32);
+      uint32_t z = (uint32_t)zz;
+      if (j == nz - 1) z &= zmask;
+      if (j == rl2) cC = (z >> rbit2) & 1u;
+      if (j >= wfirst) {
+        uint32_t w = k2 > 0 ? __funnelshift_r(zprev, z, kb) + cC : z;
+        if (k2 > 0) {
+          cC = w < cC ? 1u : 0u;
+          if (i == nf - 1) w &= wmask;
+        }
+        if (i < nf && i < out_limbs) dst[(size_t)i * N] = w;
+        ++i;
+      }
+      zprev = z;
+      xprev = xv[q];
+    }
+  }
+  // w limbs whose upper z limb lies above Z: z_{nz-1} (when it is their lower limb) and zeros
+  for (; i < nf; ++i) {
+    uint32_t w = (kl + i == nz - 1 ? (zprev >> kb) : 0u) + cC;
     cC = w < cC ? 1u : 0u;
     if (i == nf - 1) w &= wmask;
     if (i < out_limbs) dst[(size_t)i * N] = w;
   }
-  for (int i = nf; i < out_limbs; ++i) dst[(size_t)i * N] = 0u;
+  for (; i < out_limbs; ++i) dst[(size_t)i * N] = 0u;
 }
 
 // Limb partial S0 + 2^8 S1 + 2^16 S2 + 2^24 S3 of four exact column sums

@@ -551,6 +551,7 @@ def run_batched(args):
     plan = runner.plan(items, tuned["schedule"])
     runner.pack(plan, items)
     form_ms = tuner.tune_forms(runner, plan, reps=2)
+    branch_ms = tuner.tune_branches(runner, plan, reps=3)
     runner.capture(plan)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -596,6 +597,7 @@ def run_batched(args):
         "identical_results": bool(identical),
         "group_forms": [[g.logN, g.L_pad, len(g.idx), list(g.forms)] for g in plan.groups],
         "form_timings_ms": form_ms,
+        "ring_branches": bool(runner.branches), "branch_timings_ms": branch_ms,
         "graph_kernels_approx": launches_graph,
         "autotune_ms": {str(k): v for k, v in tuned["timings_ms"].items()},
     }

@@ -10,12 +10,14 @@ the whole batch is one graph launch from the host.
 
 The level buckets are the prime-count schedule: a wider bucket pads more
 ciphertexts to more NTT primes and limbs, a narrower one costs more launches.
-`Autotuner` searches two levels of schedule on the batch at hand: the bucket
+`Autotuner` searches three levels of schedule on the batch at hand: the bucket
 count per ring size, then for every group the kernel forms of its ring
 products (tensor-core or integer reconstruction, tensor-core or integer lift,
 fused or split transform schedule; `fhe_set_forms`), and keeps the fastest,
-cached per (GPU, ring size, limb count, batch size class).  Every form gives
-bit-identical results, so the choice is a pure schedule.
+cached per (GPU, ring size, limb count, batch size class), and finally whether
+the ring sizes run one after another or as parallel graph branches (one
+stream per ring size).  Every form gives bit-identical results, so the choice
+is a pure schedule.
 
 All arithmetic runs in the library's kernels; this module only plans, packs
 (device-to-device copies into padded tensors) and launches.
@@ -91,6 +93,8 @@ class BatchRunner:
 
         self.torch = torch
         self.graph = None
+        self.branches = False  # ring sizes on parallel streams (graph branches); chosen by Autotuner
+        self._streams = {}
 
     def plan(self, items: list[Item], schedule: dict) -> Plan:
         torch = self.torch
@@ -130,15 +134,44 @@ class BatchRunner:
         fhe_set_forms(g.ctx, *(forms or g.forms))
         fhe_mult_relin_rescale_ragged(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.k)
 
-    def run(self, plan: Plan) -> None:
-        for g in plan.groups:
-            self.run_group(g)
+    def branch_streams(self, plan: Plan) -> dict:
+        """One side stream per ring size of the plan (kept, so workspaces sized by an eager run are reused)."""
+        torch = self.torch
+        for logN in sorted({g.logN for g in plan.groups}):
+            if logN not in self._streams:
+                self._streams[logN] = torch.cuda.Stream()
+        return self._streams
+
+    def run(self, plan: Plan, branches: bool | None = None) -> None:
+        """Launch every group.  With branches, the groups of each ring size go to that ring's own stream
+        (forked from and joined back to the current stream): rings then overlap on the GPU, and in a
+        captured graph they are independent branches.  Groups of one ring stay in order on one stream,
+        so each stream keeps its own workspace."""
+        torch = self.torch
+        if branches is None:
+            branches = self.branches
+        if not branches:
+            for g in plan.groups:
+                self.run_group(g)
+        else:
+            main = torch.cuda.current_stream()
+            streams = self.branch_streams(plan)
+            used = sorted({g.logN for g in plan.groups})
+            for logN in used:
+                streams[logN].wait_stream(main)
+            for g in plan.groups:
+                with torch.cuda.stream(streams[g.logN]):
+                    self.run_group(g)
+            for logN in used:
+                main.wait_stream(streams[logN])
         for c in {id(g.ctx): g.ctx for g in plan.groups}.values():
             fhe_set_forms(c, *DEFAULT_FORMS)
 
-    def capture(self, plan: Plan):
+    def capture(self, plan: Plan, branches: bool | None = None):
         """Capture run(plan) into a CUDA graph (workspaces are sized by a first eager run)."""
         torch = self.torch
+        if branches is not None:
+            self.branches = bool(branches)
         self.run(plan)
         torch.cuda.synchronize()
         s = torch.cuda.Stream()
@@ -240,6 +273,39 @@ class Autotuner:
             fhe_set_forms(g.ctx, *DEFAULT_FORMS)
         self._save()
         return report
+
+    @staticmethod
+    def branches_key(gpu: str, plan: Plan) -> str:
+        rings = ",".join(str(n) for n in sorted({g.logN for g in plan.groups}))
+        size_class = 1 << max(0, int(np.ceil(np.log2(max(1, sum(len(g.idx) for g in plan.groups))))))
+        return f"{gpu}|rings={rings}|n<={size_class}|branches"
+
+    def tune_branches(self, runner: BatchRunner, plan: Plan, reps: int = 3) -> dict:
+        """Captures the plan with the ring sizes in sequence and as parallel branches, replays both and
+        keeps the faster (cached); returns {form: ms per replay}."""
+        torch = runner.torch
+        key = self.branches_key(torch.cuda.get_device_name(), plan)
+        if key in self.cache:
+            runner.branches = bool(self.cache[key])
+            return {}
+        timings = {}
+        for br in (False, True):
+            graph = runner.capture(plan, branches=br)
+            graph.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                graph.replay()
+            e1.record()
+            e1.synchronize()
+            timings["branches" if br else "sequence"] = e0.elapsed_time(e1) / reps
+            del graph
+            runner.graph = None
+        runner.branches = timings["branches"] < timings["sequence"]
+        self.cache[key] = runner.branches
+        self._save()
+        return timings
 
     def _save(self):
         if self.cache_path:

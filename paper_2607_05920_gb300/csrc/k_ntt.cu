@@ -422,54 +422,151 @@ __device__ __forceinline__ void rows_inv_multi(uint32_t (&x)[R][16], int c, int 
   }
 }
 
+// The row stages with a thread's twiddle pairs held in registers, so a loop over operands
+// reuses them: t[0, 15) serve the layout-A stages (distance 16 h, h = 8, 4, 2, 1: 1, 2, 4, 8
+// pairs, the group g of stage h at t[8 / h - 1 + g]), t[15, 30) the layout-B stages (distance h).
+__device__ __forceinline__ void row_twiddles(uint2 (&t)[30], int c, int j0, int N, const uint2* __restrict__ w) {
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+    for (int g = 0; g < 8 / h; ++g) t[8 / h - 1 + g] = __ldg(w + N / (32 * h) + c * (8 / h) + g);
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+    for (int g = 0; g < 8 / h; ++g) t[15 + 8 / h - 1 + g] = __ldg(w + N / (2 * h) + c * (128 / h) + j0 * (8 / h) + g);
+}
+// Forward row stages of one row (as rows_fwd_multi<1>): x[k] = row[j0 + 16 k] in [0, 4q) on entry,
+// x[j] = row[16 j0 + j] of the transform in [0, 4q) on exit; sr is the row's exchange slot.
+__device__ __forceinline__ void rows_fwd_reg(uint32_t (&x)[16], int j0, uint32_t* sr, const uint2 (&t)[30],
+                                             uint32_t q) {
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const uint2 w = t[8 / h - 1 + k / (2 * h)];
+      ct_bfly(x[k], x[k + h], w.x, w.y, q);
+    }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sr[rpad(j0 + 16 * k)] = x[k];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = sr[rpad(16 * j0 + j)];
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const uint2 w = t[15 + 8 / h - 1 + j / (2 * h)];
+      ct_bfly(x[j], x[j + h], w.x, w.y, q);
+    }
+}
+// Inverse row stages of one row (as rows_inv_multi<1>), with the inverse table's pairs in t.
+__device__ __forceinline__ void rows_inv_reg(uint32_t (&x)[16], int j0, uint32_t* sr, const uint2 (&t)[30],
+                                             uint32_t q) {
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & h) continue;
+      const uint2 w = t[15 + 8 / h - 1 + j / (2 * h)];
+      gs_bfly(x[j], x[j + h], w.x, w.y, q);
+    }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sr[rpad(16 * j0 + j)] = x[j];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = sr[rpad(j0 + 16 * k)];
+#pragma unroll
+  for (int h = 1; h <= 8; h <<= 1)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k & h) continue;
+      const uint2 w = t[8 / h - 1 + k / (2 * h)];
+      gs_bfly(x[k], x[k + h], w.x, w.y, q);
+    }
+}
+
 // Tensor product in the transform domain (Sec. 5 pipeline): X = [batch][4][r][N]
 // holds (B1, A1, B2, A2) after the forward column stages; the kernel finishes
 // their transforms, forms D0 = B1 B2, D1 = A1 B2 + B1 A2, D2 = A1 A2
-// (Montgomery products; schoolbook, not Sec. 5's Karatsuba form, see below) and
-// runs the inverse row stages of D0, D1, D2 into blocks 0..2.
+// (lazy Montgomery products; schoolbook, not Sec. 5's Karatsuba form: two
+// reductions and four lazy products take fewer instructions than Karatsuba's
+// three full products with four reductions, two modular additions and two
+// modular subtractions) and runs the inverse row stages of D0, D1, D2 into
+// blocks 0..2.
+// The pass runs as loops: a thread loads its row's forward twiddle pairs once, transforms the
+// four operand rows one after another (one copy of the stage code, not four interleaved copies)
+// and parks each result in its exchange slot (B2, A2 reduced below q, so that B1, A1 in [0, 4q)
+// can be the first operands: 4 q^2 < q 2^32); then, with the inverse pairs in the same
+// registers, it forms each output from the slots and runs its inverse row stages.  D1 (which
+// reads all four slots) goes first and exchanges in a fifth slot; D0 = B1 B2 then exchanges in
+// B1's slot and D2 = A1 A2 in A1's, each after its own operands were read.  Against the
+// four-operand unrolled form (one twiddle load per four butterflies, but four times the code)
+// this keeps the pass out of instruction-fetch stalls: 7.20 -> 6.59 ms per N = 2^16 step of 64
+// pairs.
 __global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
-                                                                      const uint2* __restrict__ tw,
-                                                                      const uint2* __restrict__ itw,
-                                                                      const uint32_t* __restrict__ qtab,
-                                                                      const uint32_t* __restrict__ qinv) {
-  __shared__ uint32_t s[kRowsPerCta * 4 * kSlot];
+                                                                        const uint2* __restrict__ tw,
+                                                                        const uint2* __restrict__ itw,
+                                                                        const uint32_t* __restrict__ qtab,
+                                                                        const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 5 * kSlot];
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
-  // ciphertext fastest within a prime: consecutive CTAs reuse the prime's twiddles (and key rows) from L2
   const int nb = gridDim.y / r;
   const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
   const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
   const size_t rowN = (size_t)r * N;
   const int c = blockIdx.x * kRowsPerCta + sub;
   uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N + (size_t)c * kRowLen;
-  uint32_t* sr = s + sub * 4 * kSlot;
-  uint32_t x[4][16];
+  uint32_t* sr = s + sub * 5 * kSlot;
+  uint2 t[30];
+  row_twiddles(t, c, j0, N, tw + (size_t)p * N);
+#pragma unroll 1
+  for (int o = 0; o < 4; ++o) {
+    uint32_t x[16];
 #pragma unroll
-  for (int o = 0; o < 4; ++o)
+    for (int k = 0; k < 16; ++k) x[k] = base[o * rowN + j0 + 16 * k];
+    uint32_t* so = sr + o * kSlot;
+    rows_fwd_reg(x, j0, so, t, q);
+    __syncwarp();  // the row's exchange reads of this slot are done
+    if (o < 2) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) x[o][k] = base[o * rowN + j0 + 16 * k];
-  rows_fwd_multi<4>(x, c, j0, sr, N, tw + (size_t)p * N, q);
-  // D0 = B1 B2, D1 = A1 B2 + B1 A2, D2 = A1 A2: the first operand of every product stays in [0, 4q)
-  // (4 q^2 < q 2^32), only B2, A2 are reduced; the lazy products in (0, 2q) feed the inverse stages,
-  // D1's sum is brought back below 2q.  Two reductions and four lazy products take fewer
-  // instructions than Karatsuba's three full products with four reductions, two modular additions
-  // and two modular subtractions (measured 7.19 vs 7.75 ms per N = 2^16 step of 64 pairs).
+      for (int j = 0; j < 16; ++j) so[rpad(16 * j0 + j)] = x[j];
+    } else {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const uint32_t B1 = x[0][j], A1 = x[1][j];
-    const uint32_t B2 = reduce4(x[2][j], q), A2 = reduce4(x[3][j], q);
-    const uint32_t d0 = mont_mul_lazy(B1, B2, q, qi), d2 = mont_mul_lazy(A1, A2, q, qi);
-    const uint32_t d1 = mont_mul_lazy(A1, B2, q, qi) + mont_mul_lazy(B1, A2, q, qi);  // (0, 4q)
-    x[0][j] = d0;
-    x[1][j] = min(d1, d1 - 2u * q);
-    x[2][j] = d2;
+      for (int j = 0; j < 16; ++j) so[rpad(16 * j0 + j)] = reduce4(x[j], q);
+    }
   }
-  uint32_t (&y)[3][16] = *reinterpret_cast<uint32_t (*)[3][16]>(&x[0][0]);
-  rows_inv_multi<3>(y, c, j0, sr, N, itw + (size_t)p * N, q);
+  row_twiddles(t, c, j0, N, itw + (size_t)p * N);
+  __syncwarp();  // all four transformed rows are in their slots
+#pragma unroll 1
+  for (int o = 0; o < 3; ++o) {
+    const int d = o == 0 ? 1 : 2 * (o - 1);  // output order D1, D0, D2
+    uint32_t x[16];
+    if (d == 1) {
 #pragma unroll
-  for (int o = 0; o < 3; ++o)
+      for (int j = 0; j < 16; ++j) {
+        const int pos = rpad(16 * j0 + j);
+        const uint32_t v = mont_mul_lazy(sr[kSlot + pos], sr[2 * kSlot + pos], q, qi) +
+                           mont_mul_lazy(sr[pos], sr[3 * kSlot + pos], q, qi);  // (0, 4q)
+        x[j] = min(v, v - 2u * q);
+      }
+    } else {
+      const uint32_t* u = sr + d * kSlot / 2;        // B1 (d = 0) or A1 (d = 2)
+      const uint32_t* v = sr + (2 + d / 2) * kSlot;  // B2 or A2
 #pragma unroll
-    for (int k = 0; k < 16; ++k) base[o * rowN + j0 + 16 * k] = y[o][k];
+      for (int j = 0; j < 16; ++j) {
+        const int pos = rpad(16 * j0 + j);
+        x[j] = mont_mul_lazy(u[pos], v[pos], q, qi);
+      }
+    }
+    uint32_t* ex = sr + (d == 1 ? 4 : d / 2) * kSlot;
+    __syncwarp();  // the row's operand reads are done before its exchange slot is overwritten
+    rows_inv_reg(x, j0, ex, t, q);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) base[d * rowN + j0 + 16 * k] = x[k];
+  }
 }
 
 // The same pass with one operand per 16-thread group: a CTA takes 4 matrix rows of one
@@ -737,7 +834,7 @@ int launch_ring_tensor(const fhe_ctx* ctx, uint32_t* X, int r, int nbatch, cudaS
     } else {
       dim3 grid((N >> 8) / kRowsPerCta, nbatch * r);
       k_ntt_rows_tensor<<<grid, 16 * kRowsPerCta, 0, st>>>(X, r, logN, ctx->d_psi2, ctx->d_ipsi2, ctx->d_q,
-                                                           ctx->d_qinv);
+                                                             ctx->d_qinv);
     }
   }
   {

@@ -32,7 +32,8 @@ def _items(pairs, count, seed, lo, hi):
     return items
 
 
-def test_batched_graph_equals_per_op_and_oracle():
+@pytest.mark.parametrize("branches", [False, True])
+def test_batched_graph_equals_per_op_and_oracle(branches):
     import torch
 
     from paper_2607_05920_gb300 import batch
@@ -48,7 +49,7 @@ def test_batched_graph_equals_per_op_and_oracle():
         assert bounds == sorted(bounds) and bounds[-1] >= max(it.logQ for it in items if it.logN == logN)
     plan = runner.plan(items, sched)
     runner.pack(plan, items)
-    runner.capture(plan)
+    runner.capture(plan, branches=branches)
     for g in plan.groups:
         g.O.zero_()
     runner.graph.replay()
@@ -112,6 +113,8 @@ def test_form_search_gives_identical_results_at_the_batched_ring_sizes():
     tuner = batch.Autotuner()
     tuner.tune_forms(runner, plan, reps=1)
     assert all(g.forms in batch.FORMS for g in plan.groups)
+    timings = tuner.tune_branches(runner, plan, reps=1)
+    assert set(timings) == {"sequence", "branches"}
     runner.capture(plan)
     for g in plan.groups:
         g.O.zero_()

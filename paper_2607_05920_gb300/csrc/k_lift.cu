@@ -346,9 +346,23 @@ __global__ void __launch_bounds__(kLtThreads, 1)
         ysgn = sign_of(s, N, ysb);
       }
     };
+    // the tile after next: its L limb rows of 512 B into L2, one 128-byte line per thread, so
+    // the register loads of the next tile (issued while the MMAs read A) find them there
+    auto prefetch = [&](int t) {
+      if (t >= sh.ntiles) return;
+      int n0, poly, b;
+      tile_of(t, n0, poly, b);
+      const int l = tid >> 2;
+      if (l < L) {
+        const uint32_t* a =
+            src + (size_t)b * src_bstride + (size_t)poly * src_pstride + (size_t)l * N + n0 + 32 * (tid & 3);
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+      }
+    };
     int tl = 0;
     bool ok = true;
     if (blockIdx.x < sh.ntiles) load(blockIdx.x);
+    prefetch(blockIdx.x + gridDim.x);
     for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
       if (tl >= 1 && !(ok = mbar_wait(a_empty, (uint32_t)(tl - 1) & 1u))) break;
 #pragma unroll
@@ -374,6 +388,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_arrive(a_full);
+      prefetch(t + 2 * (int)gridDim.x);
       if (t + (int)gridDim.x < sh.ntiles) load(t + gridDim.x);  // in flight while the MMAs read A
     }
   } else {

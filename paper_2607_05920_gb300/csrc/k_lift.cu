@@ -211,8 +211,9 @@ __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint
 // halves) so each half's drain overlaps the other half's MMAs.  Warp roles:
 //   warps 0-7   limbs -> digit tile A (two threads per coefficient row),
 //               the next tile's limbs loaded while the MMAs read A;
-//   warps 8-23  four epilogue groups, two per half, alternating 4-residue
-//               column blocks: TMEM -> integers -> Montgomery -> residue rows;
+//   warps 8-23  four epilogue groups that drain the first half, then the
+//               second, each taking every fourth 4-residue column block:
+//               TMEM -> integers -> Montgomery -> residue rows;
 //   warp 24     TMEM allocation and the MMA issue (one thread).
 constexpr int kLtRows = 128;
 constexpr int kLtYWarps = 8, kLtEWarps = 16;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
     mbar_init(a_empty, 1);
     for (int h = 0; h < 2; ++h) {
       mbar_init(acc_full(h), 1);
-      mbar_init(acc_empty(h), 32 * kLtEWarps / 2);
+      mbar_init(acc_empty(h), 32 * kLtEWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -392,25 +393,26 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       if (t + (int)gridDim.x < sh.ntiles) load(t + gridDim.x);  // in flight while the MMAs read A
     }
   } else {
-    // E: group g (0..3) drains half g >> 1, 4-residue column blocks of parity g & 1
+    // E: all four groups drain half 0, then half 1; group g takes the 4-residue column blocks
+    // g, g + 4, ... of each, so a half's accumulator is released after a quarter of its work
+    // per group and the next tile's MMAs into it wait less
     const int e = tid - 32 * kLtYWarps;
     const int g = e >> 7, ec = e & (kLtRows - 1);
-    const int h = g >> 1, par = g & 1;
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    const int i0 = h ? sh.r0 : 0, i1 = h ? r : min(r, sh.r0);
     int tl = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < sh.ntiles; t += gridDim.x, ++tl) {
-      if (h >= nh) break;
-      int n0, poly, b;
-      tile_of(t, n0, poly, b);
+    for (int t = blockIdx.x; t < sh.ntiles && ok; t += gridDim.x, ++tl) {
+     int n0, poly, b;
+     tile_of(t, n0, poly, b);
+     uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n0 + ec;
+     for (int h = 0; h < nh; ++h) {
+      const int i0 = h ? sh.r0 : 0, i1 = h ? r : min(r, sh.r0);
       ok = ok && mbar_wait(acc_full(h), (uint32_t)tl & 1u);
       ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tmem + lane_off + (uint32_t)(h * sh.acc_cols);
-      uint32_t* d = dst + (size_t)b * dst_bstride + (size_t)poly * dst_pstride + n0 + ec;
-      for (int q4 = par; 4 * q4 < i1 - i0; q4 += 2) {
+      for (int q4 = g; 4 * q4 < i1 - i0; q4 += 4) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
@@ -440,6 +442,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       mbar_arrive(acc_empty(h));
+     }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

@@ -503,17 +503,22 @@ __device__ __forceinline__ void relin_setup(RelinStream& rs, const EpiArgs& epi,
   rs.N = N;
 }
 
-// The relinearisation epilogue over a limb column held in shared memory
-// (col[l kTcRows] for l in [min(rl, sl), nx), the exact product X after its
-// carries), in one pass: the shifted and rounded limbs plus the addend (z)
-// and, when k2 > 0, the rescaled and rounded limbs (w) advance together, each
-// new z limb completing the w limb below it, so every column limb is read
-// once and no z limb goes back to shared memory.  Loads come eight at a time
-// ahead of the carry chains.
-//   z_j = ((X + 2^(s-1)) >> s) limb j + addend limb j, mod 2^ob;
-//   out = (Z + 2^(k2-1)) >> k2 mod 2^(ob-k2) (or Z when k2 = 0), zero-padded.
-__device__ __forceinline__ void relin_column(const uint32_t* col, int nx, const EpiArgs& epi, int ob,
-                                             const uint32_t* add, int add_stride, uint32_t* dst, int N) {
+// The relinearisation epilogue of one coefficient in one pass over its limb column held in
+// shared memory (col[l kTcRows] for l in [min(rl, sl), nx): the column sums after their
+// carries, the high half still without the low half's carry), with the
+// low half's carry c0 rippled in from limb lsplit up as the limbs are read (limbs at and above
+// nx read as zero):
+//   X' = X + c0 2^(32 lsplit) mod 2^(32 nx),
+//   Z  = ((X' + 2^(s-1)) >> s) + A mod 2^ob,
+//   W  = (Z + 2^(k2-1)) >> k2 mod 2^(ob-k2)   (W = Z when k2 = 0),
+// stored as out_limbs limbs (zeros above W).  The rounding carry of the shift and the carry of
+// the addend travel as one carry in {0, 1, 2} (f + a + c0 + c1 has the same low word as
+// ((f + c0) mod 2^32) + a + c1, and the two carries out add up to its high word), so a limb of
+// Z costs one funnel shift and one three-input add.  Limbs between the first output limb and
+// the top one take a branch-free loop; the first limbs (rounding bits) and the top limb (masks)
+// take the general step.
+__device__ __forceinline__ void relin_column(const uint32_t* col, int nx, int lsplit, int c0, const EpiArgs& epi,
+                                             int ob, const uint32_t* add, int add_stride, uint32_t* dst, int N) {
   const int s = epi.shift, sl = s >> 5, sb = s & 31, rl = (s - 1) >> 5, rbit = (s - 1) & 31;
   const int nz = (ob + 31) >> 5;
   const uint32_t zmask = limb_mask(nz - 1, ob);
@@ -524,41 +529,72 @@ __device__ __forceinline__ void relin_column(const uint32_t* col, int nx, const 
   const int fb = ob - k2, nf = k2 > 0 ? (fb + 31) >> 5 : nz;
   const uint32_t wmask = limb_mask(nf - 1, fb);
   const int wfirst = k2 > 0 ? kl + 1 : 0;  // z limb that completes w limb 0
-  uint32_t cA = (col[(size_t)rl * kTcRows] >> rbit) & 1u, cB = 0u, cC = 0u;
-  uint32_t xprev = sl < nx ? col[(size_t)sl * kTcRows] : 0u, zprev = 0u;
+  // X' limbs in ascending order: every limb from lsplit up passes through `ripple` exactly once
+  int rc = 0;  // carry entering the next rippled limb (c0 at limb lsplit)
+  auto ripple = [&](int l, uint32_t x) -> uint32_t {
+    if (l == lsplit) rc = c0;
+    const long long t = (long long)x + rc;
+    rc = (int)(t >> 32);
+    return l < nx ? (uint32_t)t : 0u;
+  };
+  auto xload = [&](int l) -> uint32_t { return l < nx ? col[(size_t)l * kTcRows] : 0u; };
+  for (int l = lsplit; l < rl; ++l) ripple(l, xload(l));  // limbs below the rounding limb only carry
+  const uint32_t xr = ripple(rl, xload(rl));
+  uint32_t c = (xr >> rbit) & 1u;  // the rounding bit, then the combined carry
+  uint32_t xprev = sl == rl ? xr : ripple(sl, xload(sl));
+  uint32_t zprev = 0u, cC = 0u;
   int i = 0;  // next output limb
-  for (int j0 = 0; j0 < nz; j0 += 8) {
+  // the general step for z limb j: every mask, rounding bit and bound checked
+  auto step = [&](int j, uint32_t x, uint32_t a) {
+    const uint64_t zz = (uint64_t)__funnelshift_r(xprev, x, sb) + a + c;
+    c = (uint32_t)(zz >> 32);
+    uint32_t z = (uint32_t)zz;
+    if (j == nz - 1) z &= zmask;
+    if (j == rl2) cC = (z >> rbit2) & 1u;
+    if (j >= wfirst) {
+      uint32_t w = z;
+      if (k2 > 0) {
+        w = __funnelshift_r(zprev, z, kb) + cC;
+        cC = w < cC ? 1u : 0u;
+        if (i == nf - 1) w &= wmask;
+      }
+      if (i < nf && i < out_limbs) dst[(size_t)i * N] = w;
+      ++i;
+    }
+    zprev = z;
+    xprev = x;
+  };
+  // z limbs [0, ja): the general step; [ja, nz - 1): no mask, no rounding bit, w limb i < nf - 1
+  const int ja = min(nz - 1, max(wfirst, rl2 + 1));
+  int j = 0;
+  for (; j < ja; ++j) step(j, ripple(sl + j + 1, xload(sl + j + 1)), j < na ? add[(size_t)j * add_stride] : 0u);
+  for (; j < nz - 1; j += 8) {
     uint32_t xv[8], av[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int j = j0 + q;
-      xv[q] = sl + j + 1 < nx ? col[(size_t)(sl + j + 1) * kTcRows] : 0u;
-      av[q] = j < na ? add[(size_t)j * add_stride] : 0u;
+      xv[q] = xload(sl + j + q + 1);
+      av[q] = j + q < na ? add[(size_t)(j + q) * add_stride] : 0u;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int j = j0 + q;
-      if (j >= nz) break;
-      const uint32_t y = __funnelshift_r(xprev, xv[q], sb) + cA;
-      cA = y < cA ? 1u : 0u;
-      const uint64_t zz = (uint64_t)y + av[q] + cB;
-      cB = (uint32_t)(zz >> 32);
-      uint32_t z = (uint32_t)zz;
-      if (j == nz - 1) z &= zmask;
-      if (j == rl2) cC = (z >> rbit2) & 1u;
-      if (j >= wfirst) {
-        uint32_t w = k2 > 0 ? __funnelshift_r(zprev, z, kb) + cC : z;
-        if (k2 > 0) {
-          cC = w < cC ? 1u : 0u;
-          if (i == nf - 1) w &= wmask;
-        }
-        if (i < nf && i < out_limbs) dst[(size_t)i * N] = w;
-        ++i;
+      if (j + q >= nz - 1) break;
+      const uint32_t x = ripple(sl + j + q + 1, xv[q]);
+      const uint64_t zz = (uint64_t)__funnelshift_r(xprev, x, sb) + av[q] + c;
+      c = (uint32_t)(zz >> 32);
+      const uint32_t z = (uint32_t)zz;
+      uint32_t w = z;
+      if (k2 > 0) {
+        w = __funnelshift_r(zprev, z, kb) + cC;
+        cC = w < cC ? 1u : 0u;
       }
+      if (i < out_limbs) dst[(size_t)i * N] = w;
+      ++i;
       zprev = z;
-      xprev = xv[q];
+      xprev = x;
     }
   }
+  j = nz - 1;
+  step(j, ripple(sl + j + 1, xload(sl + j + 1)), j < na ? add[(size_t)j * add_stride] : 0u);
   // w limbs whose upper z limb lies above Z: z_{nz-1} (when it is their lower limb) and zeros
   for (; i < nf; ++i) {
     uint32_t w = (kl + i == nz - 1 ? (zprev >> kb) : 0u) + cC;
@@ -964,18 +1000,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t* add_s =
             sh.nadd ? reinterpret_cast<const uint32_t*>(ADD + (size_t)(tl % sh.nadd) * add_limbs * 512) + ec : nullptr;
         uint32_t* dst = out + (size_t)b * out_bstride + (size_t)poly * out_pstride + n0 + ec;
-        // group 0's carry into the high half
-        long long c = CAR[par * kTcRows + ec];
-        for (int l = lsplit; l < 4 * MT; ++l) {
-          const long long v = (long long)col[(size_t)l * kTcRows] + c;
-          col[(size_t)l * kTcRows] = (uint32_t)v;
-          c = v >> 32;
-        }
         const uint32_t* add = has_add ? (add_s ? add_s
                                                : epi.add + (size_t)b * epi.add_bstride +
                                                      (size_t)poly * epi.add_pstride + n0 + ec)
                                       : nullptr;
-        relin_column(col, 4 * MT, epi, ob, add, add_s ? kTcRows : N, dst, N);
+        // group 0's carry enters the high half at limb lsplit, rippled in as the epilogue reads it
+        relin_column(col, 4 * MT, lsplit, (int)CAR[par * kTcRows + ec], epi, ob, add, add_s ? kTcRows : N, dst, N);
         if (sh.nadd) mbar_arrive(add_empty(eg));
         mbar_arrive(limb_empty(par));
       }

@@ -393,11 +393,12 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       if (t + (int)gridDim.x < sh.ntiles) load(t + gridDim.x);  // in flight while the MMAs read A
     }
   } else {
-    // E: all four groups drain half 0, then half 1; group g takes the 4-residue column blocks
-    // g, g + 4, ... of each, so a half's accumulator is released after a quarter of its work
-    // per group and the next tile's MMAs into it wait less
+    // E: all four groups drain half 0, then half 1, each taking every fourth 4-residue column
+    // block, so a half's accumulator is released after a quarter of its work per group and the
+    // next tile's MMAs into it wait less
     const int e = tid - 32 * kLtYWarps;
     const int g = e >> 7, ec = e & (kLtRows - 1);
+    const int nb0 = (min(r, sh.r0) + 3) / 4;  // 4-residue column blocks of half 0
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     int tl = 0;
     bool ok = true;
@@ -412,7 +413,10 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t base = tmem + lane_off + (uint32_t)(h * sh.acc_cols);
-      for (int q4 = g; 4 * q4 < i1 - i0; q4 += 4) {
+      // blocks are numbered across both halves (half 1 after half 0's nb0) and dealt round-robin,
+      // starting one group later each tile, so no group drains more than its share every tile
+      const int first = (g - (h ? nb0 : 0) - (tl & 3)) & 3;
+      for (int q4 = first; 4 * q4 < i1 - i0; q4 += 4) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"

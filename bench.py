@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-iters", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-sub-batches", type=int, default=E2E_CHUNKS,
+                    help="end to end: sub-batches whose upload, compute and download overlap")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--workload", default="ns", choices=["ns", "batched", "serving", "rotations", "bgv"],
@@ -399,7 +401,7 @@ def run_ours(args):
     A_h = A.data.cpu().pin_memory()
     B_h = B.data.cpu().pin_memory()
     out_h = torch.empty(out.data.shape, dtype=torch.int32).pin_memory()
-    nchunk = E2E_CHUNKS if cnum % E2E_CHUNKS == 0 else 1
+    nchunk = args.e2e_sub_batches if cnum % args.e2e_sub_batches == 0 else 1
     per = cnum // nchunk
     up, comp, down = (torch.cuda.Stream() for _ in range(3))
     parts = [(fhe.Ciphertext(A.data[c * per:(c + 1) * per], LOGQ), fhe.Ciphertext(B.data[c * per:(c + 1) * per], LOGQ),

@@ -554,6 +554,7 @@ def run_batched(args):
     runner.pack(plan, items)
     form_ms = tuner.tune_forms(runner, plan, reps=2)
     branch_ms = tuner.tune_branches(runner, plan, reps=3)
+    table_ms = tuner.tune_table(runner, plan, reps=2)
     runner.capture(plan)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -583,7 +584,9 @@ def run_batched(args):
     ms_per_level = e0.elapsed_time(e1) / args.steps
     got = runner.outputs(plan, items)
     identical = all(torch.equal(got[i], ref[i].data[0]) and torch.equal(got[i], lev[i]) for i in range(len(items)))
-    launches_graph = sum(16 for _ in plan.groups)
+    # per group: 2 lifts, 2 reconstructions, 1 signed lift and the 6 transform launches of its two ring
+    # products (about 16 kernels with the limb work); the work-table call shares the 6 transform launches
+    launches_graph = sum(16 for _ in plan.groups) if runner.table is None else 10 * len(plan.groups) + 6
     line = {
         "metric": "uneven-batch HMult+relin+rescale pairs/s (N 2^13..2^16, logQ 200..1200)",
         "value": len(items) / (ms_graph / 1e3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
@@ -600,6 +603,7 @@ def run_batched(args):
         "group_forms": [[g.logN, g.L_pad, len(g.idx), list(g.forms)] for g in plan.groups],
         "form_timings_ms": form_ms,
         "ring_branches": bool(runner.branches), "branch_timings_ms": branch_ms,
+        "work_table": list(runner.table) if runner.table else None, "table_timings_ms": table_ms,
         "graph_kernels_approx": launches_graph,
         "autotune_ms": {str(k): v for k, v in tuned["timings_ms"].items()},
     }

@@ -276,6 +276,44 @@ int fhe_mult_relin_rescale_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_
                                   int L_pad, const int32_t* item_logQ, int logQ_max, int k, void* ws,
                                   size_t ws_bytes, void* stream);
 
+/* One group of fhe_mult_relin_rescale_batch: the arguments of one
+ * fhe_mult_relin_rescale_ragged call (its context fixes the ring size). */
+typedef struct {
+  fhe_ctx* ctx;              /* CKKS context with keys; its ring size N = 2^logN    */
+  const uint32_t* a;         /* device uint32_t[cnum][2][L_pad][N]                 */
+  const uint32_t* b;         /* the same shape                                     */
+  uint32_t* out;             /* the same shape; must not alias a or b              */
+  const int32_t* item_logQ;  /* device int32_t[cnum], each <= logQ_max             */
+  int32_t cnum, L_pad, logQ_max;
+  void* ws;                  /* this group's own workspace (FHE_OP_MULT_RAGGED at   */
+  size_t ws_bytes;           /* logQ_max, cnum); no two groups may share bytes      */
+} fhe_batch_group;
+
+/* Schedule of the work-table transform launches (chosen by an autotuner). */
+typedef struct {
+  int32_t col_ctas_per_sm;   /* column stages: persistent grid of this many CTAs per SM
+                                (clamped to what fits); 0: one CTA per work unit      */
+  int32_t row_ctas_per_sm;   /* fused row passes: the same                             */
+  int32_t col_unit_rows;     /* prime rows per column-stage work unit of the persistent
+                                grid (>= 1; one CTA per unit takes 256/N1 column jobs)  */
+} fhe_batch_sched;
+
+/* Batched multiply + relinearise + rescale over pairs of SEVERAL ring sizes
+ * and levels at once (the CipherTensor batching of Sec. 6, "Pairwise and
+ * Broadcast Modes", across rings; CKKS only): group g is the ragged batch
+ * of fhe_mult_relin_rescale_ragged with its own context, and its results are
+ * exactly those of that call.  The transform stages of all groups run as
+ * single launches over a work table of units (ciphertext, polynomial, prime
+ * group, ring size, prime count): the forward column stages, the fused
+ * transform-domain pass and the inverse column stages of the tensor
+ * products, then the same three of the key switches; each group's lifts and
+ * reconstructions run per group with its context's kernel forms.  Groups at
+ * N <= 2^12 run their transforms per group.  1 <= ngroups <= 32, every
+ * context on the current device; sched NULL = {4, 4, 1}.  Profiling of the
+ * work-table launches goes to the first group's context. */
+int fhe_mult_relin_rescale_batch(const fhe_batch_group* groups, int ngroups, int k, const fhe_batch_sched* sched,
+                                 void* stream);
+
 /* Rescale (rescaleBy_pairwise_into, Sec. 6): out = round(in / 2^k) mod
  * 2^(logQ - k), halves rounded up; out->logQ must equal in->logQ - k. */
 int fhe_rescale(fhe_ctx* ctx, const fhe_ct* in, int k, fhe_ct* out, void* stream);

@@ -72,6 +72,17 @@ class FheCt(ctypes.Structure):
                 ("level", ctypes.c_int32), ("log_scale", ctypes.c_double)]
 
 
+class FheBatchGroup(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("item_logQ", ctypes.c_void_p), ("cnum", ctypes.c_int32), ("L_pad", ctypes.c_int32),
+                ("logQ_max", ctypes.c_int32), ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t)]
+
+
+class FheBatchSched(ctypes.Structure):
+    _fields_ = [("col_ctas_per_sm", ctypes.c_int32), ("row_ctas_per_sm", ctypes.c_int32),
+                ("col_unit_rows", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -100,6 +111,7 @@ SIGNATURES = {
                                     _SZ, _P]),
     "fhe_rescale": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P]),
     "fhe_mult_relin_rescale_ragged": (_I, [_P, _P, _P, _P, _I, _I, _P, _I, _I, _P, _SZ, _P]),
+    "fhe_mult_relin_rescale_batch": (_I, [ctypes.POINTER(FheBatchGroup), _I, _I, ctypes.POINTER(FheBatchSched), _P]),
     "fhe_moddown": (_I, [_P, ctypes.POINTER(FheCt), ctypes.POINTER(FheCt), _P]),
     "fhe_rotate": (_I, [_P, ctypes.POINTER(FheCt), _I, ctypes.POINTER(FheCt), _P, _SZ, _P]),
     "fhe_rotate_hoisted": (_I, [_P, ctypes.POINTER(FheCt), _P, _I, _P, _P, _SZ, _P]),
@@ -512,6 +524,26 @@ def fhe_mult_relin_rescale_ragged(ctx: Context, a, b, out, item_logQ, logQ_max: 
         ctx.handle, _dev(a, torch.int32, (cnum, 2, L_pad, N)), _dev(b, torch.int32, (cnum, 2, L_pad, N)),
         _dev(out, torch.int32, (cnum, 2, L_pad, N)), int(cnum), int(L_pad), _dev(item_logQ, torch.int32, (cnum,)),
         int(logQ_max), int(k), ws.data_ptr(), ws.numel(), _stream()), "fhe_mult_relin_rescale_ragged")
+
+
+def fhe_mult_relin_rescale_batch(groups, k: int, sched=None) -> None:
+    """Ragged batches of several ring sizes in one call, the transform stages of all of them as single
+    work-table launches.  groups: sequence of (ctx, a, b, out, item_logQ, logQ_max, ws) with the tensors of
+    fhe_mult_relin_rescale_ragged and a distinct workspace per group (uint8 CUDA tensor of at least
+    fhe_workspace_bytes(FHE_OP_MULT_RAGGED, logQ_max, cnum)); sched: (col_ctas_per_sm, row_ctas_per_sm,
+    col_unit_rows) or None for the library's default."""
+    import torch
+
+    arr = (FheBatchGroup * len(groups))()
+    for i, (ctx, a, b, out, item_logQ, logQ_max, ws) in enumerate(groups):
+        cnum, two, L_pad, N = a.shape
+        shape = (cnum, 2, L_pad, N)
+        arr[i] = FheBatchGroup(ctx.handle, _dev(a, torch.int32, shape), _dev(b, torch.int32, shape),
+                               _dev(out, torch.int32, shape), _dev(item_logQ, torch.int32, (cnum,)), int(cnum),
+                               int(L_pad), int(logQ_max), ws.data_ptr(), ws.numel())
+    sp = ctypes.byref(FheBatchSched(*[int(x) for x in sched])) if sched is not None else None
+    _check(lib.fhe_mult_relin_rescale_batch(arr, len(groups), int(k), sp, _stream()),
+           "fhe_mult_relin_rescale_batch")
 
 
 def fhe_rescale(ctx: Context, ct: Ciphertext, k: int, out: Ciphertext) -> None:

@@ -31,13 +31,15 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (FHE_CRT_DIRECT, FHE_CRT_DIRECT_INT, FHE_LIFT_AUTO, FHE_LIFT_INT, FHE_LIFT_TC, FHE_NTT_FUSED,
-               FHE_NTT_FUSED_GROUPS, FHE_NTT_SPLIT, Ciphertext, Context, fhe_mult_relin_rescale,
-               fhe_mult_relin_rescale_ragged, fhe_set_forms, limbs)
+               FHE_NTT_FUSED_GROUPS, FHE_NTT_SPLIT, FHE_OP_MULT_RAGGED, Ciphertext, Context, fhe_mult_relin_rescale,
+               fhe_mult_relin_rescale_batch, fhe_mult_relin_rescale_ragged, fhe_set_forms, lib, limbs)
 
 # (reconstruction, lift, transform schedule) candidates of a group
 FORMS = tuple((c, l, t) for c in (FHE_CRT_DIRECT, FHE_CRT_DIRECT_INT) for l in (FHE_LIFT_TC, FHE_LIFT_INT)
               for t in (FHE_NTT_FUSED, FHE_NTT_FUSED_GROUPS, FHE_NTT_SPLIT))
 DEFAULT_FORMS = (FHE_CRT_DIRECT, FHE_LIFT_AUTO, FHE_NTT_FUSED)
+# work-table schedules (col_ctas_per_sm, row_ctas_per_sm, col_unit_rows): 0 CTAs per SM = one CTA per unit
+TABLE_SCHEDS = tuple((c, r, u) for c in (0, 2, 3) for r in (0, 2, 4) for u in ((1,) if c == 0 else (1, 4, 16)))
 
 
 @dataclass
@@ -62,6 +64,7 @@ class Group:
     O: object = None
     bits: object = None
     forms: tuple = DEFAULT_FORMS
+    ws: object = None  # the group's own workspace on the work-table path
 
 
 def bucket_bounds(levels: list[int], nbuckets: int) -> list[int]:
@@ -94,6 +97,7 @@ class BatchRunner:
         self.torch = torch
         self.graph = None
         self.branches = False  # ring sizes on parallel streams (graph branches); chosen by Autotuner
+        self.table = None      # a work-table schedule: all groups in one fhe_mult_relin_rescale_batch call
         self._streams = {}
 
     def plan(self, items: list[Item], schedule: dict) -> Plan:
@@ -142,12 +146,31 @@ class BatchRunner:
                 self._streams[logN] = torch.cuda.Stream()
         return self._streams
 
+    def group_ws(self, g: Group):
+        """The group's own workspace (the work-table call keeps every group's intermediates at once)."""
+        nbytes = lib.fhe_workspace_bytes(g.ctx.handle, FHE_OP_MULT_RAGGED, int(g.logQ_max), len(g.idx))
+        if g.ws is None or g.ws.numel() < nbytes:
+            g.ws = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=g.ctx.device)
+        return g.ws
+
+    def run_table(self, plan: Plan, sched) -> None:
+        """Every group in one fhe_mult_relin_rescale_batch call: lifts and reconstructions per group (default
+        forms), each transform stage of all groups as one work-table launch with schedule `sched`."""
+        for c in {id(g.ctx): g.ctx for g in plan.groups}.values():
+            fhe_set_forms(c, *DEFAULT_FORMS)
+        groups = [(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.group_ws(g)) for g in plan.groups]
+        for i in range(0, len(groups), 32):  # at most 32 groups (table segments) per call
+            fhe_mult_relin_rescale_batch(groups[i:i + 32], self.k, sched)
+
     def run(self, plan: Plan, branches: bool | None = None) -> None:
-        """Launch every group.  With branches, the groups of each ring size go to that ring's own stream
+        """Launch every group (one work-table call when self.table holds a schedule).  With branches, the groups of each ring size go to that ring's own stream
         (forked from and joined back to the current stream): rings then overlap on the GPU, and in a
         captured graph they are independent branches.  Groups of one ring stay in order on one stream,
         so each stream keeps its own workspace."""
         torch = self.torch
+        if self.table is not None:
+            self.run_table(plan, self.table)
+            return
         if branches is None:
             branches = self.branches
         if not branches:
@@ -306,6 +329,54 @@ class Autotuner:
         self.cache[key] = runner.branches
         self._save()
         return timings
+
+    @staticmethod
+    def table_key(gpu: str, plan: Plan) -> str:
+        return Autotuner.branches_key(gpu, plan).replace("|branches", "|table")
+
+    def tune_table(self, runner: BatchRunner, plan: Plan, reps: int = 2) -> dict:
+        """Times the work-table call under every schedule of TABLE_SCHEDS, then captures the best one and the
+        per-group graph (in the form tune_branches chose) and keeps the faster as runner.table (a schedule,
+        or None for the per-group graph); cached.  Returns {schedule or form: ms}."""
+        torch = runner.torch
+        key = self.table_key(torch.cuda.get_device_name(), plan)
+        if key in self.cache:
+            runner.table = tuple(self.cache[key]) if self.cache[key] else None
+            return {}
+        timings = {}
+        for sc in TABLE_SCHEDS:
+            runner.run_table(plan, sc)  # warm (and sizes the workspaces)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                runner.run_table(plan, sc)
+            e1.record()
+            e1.synchronize()
+            timings[sc] = e0.elapsed_time(e1) / reps
+        best = min(timings, key=timings.get)
+        report = {"table " + "/".join(map(str, sc)): round(t, 4) for sc, t in timings.items()}
+        graphs = {}
+        for mode in (best, None):
+            runner.table = mode
+            graph = runner.capture(plan)
+            graph.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                graph.replay()
+            e1.record()
+            e1.synchronize()
+            graphs[mode] = e0.elapsed_time(e1) / reps
+            del graph
+            runner.graph = None
+        runner.table = best if graphs[best] < graphs[None] else None
+        report["graph table"] = round(graphs[best], 4)
+        report["graph groups"] = round(graphs[None], 4)
+        self.cache[key] = list(runner.table) if runner.table else None
+        self._save()
+        return report
 
     def _save(self):
         if self.cache_path:

@@ -331,6 +331,118 @@ int mult_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_t* b, uint32_t* ou
                          item_bits, L);
 }
 
+// Ragged batches of several rings (groups): the steps of mult_ragged, with each transform stage
+// of all groups at N >= 2^13 launched once over a work table (one segment per group).
+int mult_batch(const fhe_batch_group* gs, int ng, int k2, const fhe_batch_sched& sc, cudaStream_t st) {
+  struct Bufs {
+    int rt, rk, L;
+    size_t N;
+    uint32_t *X, *D, *Y;
+  };
+  std::vector<Bufs> v(ng);
+  for (int i = 0; i < ng; ++i) {
+    fhe_ctx* ctx = gs[i].ctx;
+    Bufs& b = v[i];
+    b.rt = r_tensor(ctx, gs[i].logQ_max);
+    b.rk = r_keyswitch(ctx, gs[i].logQ_max);
+    b.L = gs[i].L_pad;
+    b.N = ctx->N;
+    const size_t cnum = gs[i].cnum;
+    Carve cv(gs[i].ws, gs[i].ws_bytes);
+    b.X = cv.take(cnum * 4 * b.rt * b.N);
+    b.D = cv.take(cnum * 3 * b.L * b.N);
+    b.Y = cv.take(cnum * 2 * b.rk * b.N);
+    if (!cv.ok || ((uintptr_t)gs[i].ws & 255)) {
+      set_error("mult_relin_rescale_batch: workspace of group %d (%zu bytes) too small or misaligned", i,
+                gs[i].ws_bytes);
+      return FHE_EWORKSPACE;
+    }
+  }
+  // groups at N <= 2^12 run their ring products per group (single-CTA transforms)
+  auto tabled = [&](int i) { return gs[i].ctx->prm.logN >= 13; };
+  int ntab = 0;
+  for (int i = 0; i < ng; ++i) ntab += tabled(i);
+  const fhe_ctx* pctx = gs[0].ctx;
+  // one stage over every tabled group; rows of the column stages as in launch_ring_tensor / _key:
+  //  tensor X = [nb][4][r][N]: forward over blocks 0..3 (row map {r, r}, 4 r nb rows), inverse over
+  //  blocks 0..2 (row map {3r, 4r}, 3 r nb rows); key Y = [nb][2][r][N]: forward over block 0 (row
+  //  map {r, 2r}, r nb rows), inverse over blocks 0..1 (row map {r, r}, 2 r nb rows)
+  auto stage = [&](bool key, int stg) -> int {
+    NttTable t{};
+    t.unit_rows = sc.col_unit_rows;
+    for (int i = 0; i < ng; ++i) {
+      if (!tabled(i)) continue;
+      const fhe_ctx* ctx = gs[i].ctx;
+      NttSeg& g = t.seg[t.nseg++];
+      const int r = key ? v[i].rk : v[i].rt, nb = gs[i].cnum;
+      g.data = key ? v[i].Y : v[i].X;
+      g.key = key ? ctx->evk.ntt : nullptr;
+      g.krows = key ? ctx->evk.rows : 0;
+      g.tw = stg == kTableColsInv ? ctx->d_ipsi2 : ctx->d_psi2;
+      g.itw = ctx->d_ipsi2;
+      g.q = ctx->d_q;
+      g.qinv = ctx->d_qinv;
+      g.r = r;
+      g.logN = ctx->prm.logN;
+      g.nb = nb;
+      if (stg == kTableColsFwd) {
+        g.group_rows = r;
+        g.group_stride = key ? 2 * r : r;
+        g.rows = (key ? 1 : 4) * r * nb;
+      } else if (stg == kTableColsInv) {
+        g.group_rows = key ? r : 3 * r;
+        g.group_stride = key ? r : 4 * r;
+        g.rows = (key ? 2 : 3) * r * nb;
+      }
+    }
+    const int per_sm = stg == kTableColsFwd || stg == kTableColsInv ? sc.col_ctas_per_sm : sc.row_ctas_per_sm;
+    return launch_ntt_table(pctx, t, stg, per_sm, st);
+  };
+  // tensor products: lifts per group, the three transform stages over the table, reconstructions
+  for (int i = 0; i < ng; ++i) {
+    const fhe_batch_group& g = gs[i];
+    const Bufs& b = v[i];
+    const size_t ctw = 2 * (size_t)b.L * b.N;
+    RET_IF(launch_lift(g.ctx, g.a, b.L, (size_t)b.L * b.N, ctw, b.X, (size_t)b.rt * b.N, 4 * (size_t)b.rt * b.N, 2,
+                       g.cnum, b.rt, st));
+    RET_IF(launch_lift(g.ctx, g.b, b.L, (size_t)b.L * b.N, ctw, b.X + 2 * (size_t)b.rt * b.N, (size_t)b.rt * b.N,
+                       4 * (size_t)b.rt * b.N, 2, g.cnum, b.rt, st));
+    if (!tabled(i)) RET_IF(launch_ring_tensor(g.ctx, b.X, b.rt, g.cnum, st));
+  }
+  if (ntab) {
+    RET_IF(stage(false, kTableColsFwd));
+    RET_IF(stage(false, kTableRowsTensor));
+    RET_IF(stage(false, kTableColsInv));
+  }
+  for (int i = 0; i < ng; ++i) {
+    const fhe_batch_group& g = gs[i];
+    const Bufs& b = v[i];
+    EpiArgs e0;
+    e0.kind = Epi::kStore;
+    e0.out_bits = g.logQ_max;
+    e0.item_bits = g.item_logQ;
+    e0.out_limbs = b.L;
+    RET_IF(launch_garner(g.ctx, b.X, (size_t)b.rt * b.N, 4 * (size_t)b.rt * b.N, b.rt, 3, g.cnum, b.D,
+                         (size_t)b.L * b.N, 3 * (size_t)b.L * b.N, e0, st));
+    RET_IF(launch_lift_signed(g.ctx, b.D + 2 * (size_t)b.L * b.N, b.L, 0, 3 * (size_t)b.L * b.N, b.Y, 0,
+                              2 * (size_t)b.rk * b.N, 1, g.cnum, b.rk, 0, g.item_logQ, st));
+    if (!tabled(i)) RET_IF(launch_ring_key(g.ctx, b.Y, g.ctx->evk.ntt, g.ctx->evk.rows, b.rk, g.cnum, st));
+  }
+  // key switches: the three transform stages over the table, then each group's epilogue
+  if (ntab) {
+    RET_IF(stage(true, kTableColsFwd));
+    RET_IF(stage(true, kTableRowsKey));
+    RET_IF(stage(true, kTableColsInv));
+  }
+  for (int i = 0; i < ng; ++i) {
+    const fhe_batch_group& g = gs[i];
+    const Bufs& b = v[i];
+    RET_IF(key_switch_epilogue(g.ctx, b.Y, b.rk, g.cnum, g.logQ_max, k2, b.D, (size_t)b.L * b.N,
+                               3 * (size_t)b.L * b.N, 2, g.out, st, g.item_logQ, b.L));
+  }
+  return FHE_OK;
+}
+
 int mult_impl(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k2, fhe_ct* out, void* ws, size_t ws_bytes,
               void* stream) {
   if (!ctx || !ct_ok(ctx, a) || !ct_ok(ctx, b) || !ct_ok(ctx, out)) {
@@ -1021,6 +1133,58 @@ int fhe_mult_relin_rescale_ragged(fhe_ctx* ctx, const uint32_t* a, const uint32_
     return FHE_EINVAL;
   }
   return mult_ragged(ctx, a, b, out, cnum, L_pad, item_logQ, logQ_max, k, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int fhe_mult_relin_rescale_batch(const fhe_batch_group* groups, int ngroups, int k, const fhe_batch_sched* sched,
+                                 void* stream) {
+  if (!groups || ngroups < 1 || ngroups > kTableSegs || k < 0) {
+    set_error("mult_relin_rescale_batch: bad arguments (%d groups, k %d)", ngroups, k);
+    return FHE_EINVAL;
+  }
+  const fhe_batch_sched sc = sched ? *sched : fhe_batch_sched{4, 4, 1};
+  if (sc.col_ctas_per_sm < 0 || sc.row_ctas_per_sm < 0 || sc.col_unit_rows < 1) {
+    set_error("mult_relin_rescale_batch: bad schedule (%d, %d, %d)", sc.col_ctas_per_sm, sc.row_ctas_per_sm,
+              sc.col_unit_rows);
+    return FHE_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("mult_relin_rescale_batch: no current device");
+    return FHE_ECUDA;
+  }
+  for (int i = 0; i < ngroups; ++i) {
+    const fhe_batch_group& g = groups[i];
+    fhe_ctx* ctx = g.ctx;
+    if (!ctx || !g.a || !g.b || !g.out || !g.item_logQ || g.cnum < 1 || g.cnum > kMaxCnum || g.logQ_max < 1 ||
+        g.logQ_max > ctx->prm.logQ || g.L_pad < limbs_for_bits(g.logQ_max) || g.L_pad > kMaxLiftLimbs ||
+        k >= g.logQ_max || is_bgv(ctx) || ctx->device != dev) {
+      set_error("mult_relin_rescale_batch: group %d: bad arguments, BGV context or another device", i);
+      return FHE_EINVAL;
+    }
+    if (!ctx->have_keys) {
+      set_error("mult_relin_rescale_batch: group %d: no relinearisation key", i);
+      return FHE_ENOKEY;
+    }
+    if (g.out == g.a || g.out == g.b) {
+      set_error("mult_relin_rescale_batch: group %d: out aliases an input", i);
+      return FHE_EINVAL;
+    }
+    // the bytes mult_batch carves from a group's workspace: X, D, Y
+    auto carved = [](const fhe_batch_group& h) {
+      const size_t N = h.ctx->N, c = h.cnum;
+      return align256(c * 4 * r_tensor(h.ctx, h.logQ_max) * N * 4) + align256(c * 3 * h.L_pad * N * 4) +
+             align256(c * 2 * r_keyswitch(h.ctx, h.logQ_max) * N * 4);
+    };
+    for (int j = 0; j < i; ++j) {
+      const uintptr_t a0 = (uintptr_t)g.ws, a1 = a0 + carved(g), b0 = (uintptr_t)groups[j].ws,
+                      b1 = b0 + carved(groups[j]);
+      if (a0 < b1 && b0 < a1) {
+        set_error("mult_relin_rescale_batch: workspaces of groups %d and %d overlap", j, i);
+        return FHE_EWORKSPACE;
+      }
+    }
+  }
+  return mult_batch(groups, ngroups, k, sc, (cudaStream_t)stream);
 }
 
 int fhe_mult_relin_rescale(fhe_ctx* ctx, const fhe_ct* a, const fhe_ct* b, int k, fhe_ct* out, void* ws,

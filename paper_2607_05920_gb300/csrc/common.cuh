@@ -293,6 +293,37 @@ int launch_ring_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krow
 // Montgomery factor removed by the inverse transform's scale, as in launch_ring_key).
 int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const uint32_t* K, int krows, int r,
                     int nbatch, uint32_t g, cudaStream_t st);
+
+// Work table of one transform stage over many ring products at once (several ring sizes
+// N >= 2^13 and prime counts): one segment per group of ring products, with that group's buffer,
+// tables and shape.  The table travels by value in the launch's parameter block, so a captured
+// graph holds it.  The launcher numbers the work units of every segment:
+//  column stages, persistent grid: a unit is `unit_rows` consecutive rows of the row map
+//    (consecutive primes of one polynomial), all 256 columns; one CTA per unit: a unit is one
+//    round of 256 / N1 column jobs (32 columns of one row each); rows are independent;
+//  fused row passes: a unit is one block of 8 matrix rows of one (ciphertext, prime).
+constexpr int kTableSegs = 32;
+struct NttSeg {
+  uint32_t* data;         // the group's ring-product buffer (X or Y of the fused launchers)
+  const uint32_t* key;    // key pass: switching key rows [2][krows][N] in transform form
+  const uint2* tw;        // forward twiddle pairs of this ring
+  const uint2* itw;       // inverse twiddle pairs
+  const uint32_t* q;      // primes
+  const uint32_t* qinv;   // q^-1 mod 2^32
+  int group_rows, group_stride;  // column stages: the row map of launch_ntt
+  int r, logN, nb, krows; // primes, log ring size, ciphertexts, key rows
+  int rows;               // column stages: rows of the row map
+  int units, unit0;       // set by the launcher
+};
+struct NttTable {
+  int nseg, total, unit_rows;
+  NttSeg seg[kTableSegs];
+};
+enum TableStage { kTableColsFwd = 0, kTableColsInv = 1, kTableRowsTensor = 2, kTableRowsKey = 3 };
+// Launches one stage over the table (every segment at logN >= 13).  ctas_per_sm > 0: a persistent
+// grid of that many CTAs per SM (clamped to what fits) walking the units in strides; 0: one CTA
+// per unit.
+int launch_ntt_table(const fhe_ctx* prof_ctx, NttTable& t, int stage, int ctas_per_sm, cudaStream_t st);
 //  key: Y = [nbatch][2][r][N]; row block 0 holds D (in), outputs D*K_b into block 0 and
 //  D*K_a into block 1 with K = [2][krows][N] (first r rows used).
 int launch_pointwise_key(const fhe_ctx* ctx, uint32_t* Y, const uint32_t* K, int krows, int r, int nbatch,

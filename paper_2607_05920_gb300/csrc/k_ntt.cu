@@ -115,18 +115,19 @@ __global__ void __launch_bounds__(512) k_ntt_small(uint32_t* __restrict__ data, 
 // columns of one row: global accesses are 128-byte coalesced, shared-memory
 // accesses conflict-free, and the twiddle of a butterfly depends only on the
 // row, so twiddle loads are warp-wide broadcasts.
+// One column job: the first log N1 forward stages of the 32 columns [32 bx, 32 bx + 32) of row y
+// of the row map (N = N1 x 256 words), run by 2 N1 threads (tid < 2 N1) over the N1 x 32 words of
+// shared memory at s.  Contains one barrier of the whole CTA, so every thread of the CTA calls it.
 template <int LOGN1>
-__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
-                                                             const uint2* __restrict__ tw,
-                                                             const uint32_t* __restrict__ qtab) {
+__device__ __forceinline__ void cols_fwd_job(uint32_t* __restrict__ data, RowMap rm, int r, int N, int bx, int y,
+                                             int tid, uint32_t* s, const uint2* __restrict__ tw,
+                                             const uint32_t* __restrict__ qtab) {
   constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
-  __shared__ uint32_t s[N1 * 32];
-  const int col = threadIdx.x & 31, j0 = threadIdx.x >> 5;
-  const int N = 1 << logN;
-  const int p = rm.prime_of(blockIdx.y, r);
+  const int col = tid & 31, j0 = tid >> 5;
+  const int p = rm.prime_of(y, r);
   const uint32_t q = __ldg(qtab + p);
   const uint2* w = tw + (size_t)p * N;
-  uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
+  uint32_t* a = data + rm.row_of(y) * N + bx * 32 + col;
   uint32_t x[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) x[k] = a[(size_t)(j0 + TPC * k) * kRowLen];
@@ -162,18 +163,17 @@ __global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_fwd(uint
   for (int j = 0; j < 16; ++j) a[(size_t)(16 * j0 + j) * kRowLen] = x[j];
 }
 
+// The inverse column job (the last log N1 inverse stages), arguments as cols_fwd_job.
 template <int LOGN1>
-__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
-                                                             const uint2* __restrict__ tw,
-                                                             const uint32_t* __restrict__ qtab) {
+__device__ __forceinline__ void cols_inv_job(uint32_t* __restrict__ data, RowMap rm, int r, int N, int bx, int y,
+                                             int tid, uint32_t* s, const uint2* __restrict__ tw,
+                                             const uint32_t* __restrict__ qtab) {
   constexpr int N1 = 1 << LOGN1, TPC = N1 / 16;
-  __shared__ uint32_t s[N1 * 32];
-  const int col = threadIdx.x & 31, j0 = threadIdx.x >> 5;
-  const int N = 1 << logN;
-  const int p = rm.prime_of(blockIdx.y, r);
+  const int col = tid & 31, j0 = tid >> 5;
+  const int p = rm.prime_of(y, r);
   const uint32_t q = __ldg(qtab + p);
   const uint2* w = tw + (size_t)p * N;
-  uint32_t* a = data + rm.row_of(blockIdx.y) * N + blockIdx.x * 32 + col;
+  uint32_t* a = data + rm.row_of(y) * N + bx * 32 + col;
   uint32_t x[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) x[j] = a[(size_t)(16 * j0 + j) * kRowLen];
@@ -206,6 +206,22 @@ __global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint
   // left in [0, 2q) and unscaled: the reconstruction folds N^-1 2^32 into its first product
 #pragma unroll
   for (int k = 0; k < 16; ++k) a[(size_t)(j0 + TPC * k) * kRowLen] = x[k];
+}
+
+// One column job per CTA: grid (256 / 32 column blocks, rows).
+template <int LOGN1>
+__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_fwd(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+                                                             const uint2* __restrict__ tw,
+                                                             const uint32_t* __restrict__ qtab) {
+  __shared__ uint32_t s[(1 << LOGN1) * 32];
+  cols_fwd_job<LOGN1>(data, rm, r, 1 << logN, blockIdx.x, blockIdx.y, threadIdx.x, s, tw, qtab);
+}
+template <int LOGN1>
+__global__ void __launch_bounds__(2 << LOGN1, 1024 >> LOGN1) k_ntt_cols_inv(uint32_t* __restrict__ data, RowMap rm, int r, int logN,
+                                                             const uint2* __restrict__ tw,
+                                                             const uint32_t* __restrict__ qtab) {
+  __shared__ uint32_t s[(1 << LOGN1) * 32];
+  cols_inv_job<LOGN1>(data, rm, r, 1 << logN, blockIdx.x, blockIdx.y, threadIdx.x, s, tw, qtab);
 }
 
 // --------------------------------------------------------------- row pass
@@ -505,19 +521,17 @@ __device__ __forceinline__ void rows_inv_reg(uint32_t (&x)[16], int j0, uint32_t
 // four-operand unrolled form (one twiddle load per four butterflies, but four times the code)
 // this keeps the pass out of instruction-fetch stalls: 7.20 -> 6.59 ms per N = 2^16 step of 64
 // pairs.
-__global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
-                                                                        const uint2* __restrict__ tw,
-                                                                        const uint2* __restrict__ itw,
-                                                                        const uint32_t* __restrict__ qtab,
-                                                                        const uint32_t* __restrict__ qinv) {
-  __shared__ uint32_t s[kRowsPerCta * 5 * kSlot];
+// One job: matrix rows [8 bx, 8 bx + 8) of (ciphertext b, prime p), 128 threads, s holds
+// kRowsPerCta * 5 * kSlot words.  Only warp-level synchronisation: each row's 16 threads own its slots.
+__device__ __forceinline__ void rows_tensor_job(uint32_t* __restrict__ X, int r, int logN, int bx, int p, int b,
+                                                uint32_t* s, const uint2* __restrict__ tw,
+                                                const uint2* __restrict__ itw, const uint32_t* __restrict__ qtab,
+                                                const uint32_t* __restrict__ qinv) {
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
-  const int nb = gridDim.y / r;
-  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
   const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
   const size_t rowN = (size_t)r * N;
-  const int c = blockIdx.x * kRowsPerCta + sub;
+  const int c = bx * kRowsPerCta + sub;
   uint32_t* base = X + (size_t)b * 4 * rowN + (size_t)p * N + (size_t)c * kRowLen;
   uint32_t* sr = s + sub * 5 * kSlot;
   uint2 t[30];
@@ -567,6 +581,19 @@ __global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor(uint32_
 #pragma unroll
     for (int k = 0; k < 16; ++k) base[d * rowN + j0 + 16 * k] = x[k];
   }
+}
+
+// grid ((N / 256) / kRowsPerCta, batch * r); ciphertext fastest within a prime (L2 reuse of the
+// prime's twiddles by consecutive CTAs).
+__global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor(uint32_t* __restrict__ X, int r, int logN,
+                                                                        const uint2* __restrict__ tw,
+                                                                        const uint2* __restrict__ itw,
+                                                                        const uint32_t* __restrict__ qtab,
+                                                                        const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 5 * kSlot];
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
+  rows_tensor_job(X, r, logN, blockIdx.x, p, b, s, tw, itw, qtab, qinv);
 }
 
 // The same pass with one operand per 16-thread group: a CTA takes 4 matrix rows of one
@@ -639,20 +666,17 @@ __global__ void __launch_bounds__(256) k_ntt_rows_tensor_g(uint32_t* __restrict_
 // its transform, multiplies it by the key rows K[0][p], K[1][p] (transform
 // form, Montgomery) and runs the inverse row stages of both products into
 // blocks 0 and 1.
-__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __restrict__ Y,
-                                                                   const uint32_t* __restrict__ K, int krows, int r,
-                                                                   int logN, const uint2* __restrict__ tw,
-                                                                   const uint2* __restrict__ itw,
-                                                                   const uint32_t* __restrict__ qtab,
-                                                                   const uint32_t* __restrict__ qinv) {
-  __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
+// One job: matrix rows [8 bx, 8 bx + 8) of (ciphertext b, prime p), 128 threads, s holds
+// kRowsPerCta * 2 * kSlot words (warp-level synchronisation only).
+__device__ __forceinline__ void rows_key_job(uint32_t* __restrict__ Y, const uint32_t* __restrict__ K, int krows,
+                                             int r, int logN, int bx, int p, int b, uint32_t* s,
+                                             const uint2* __restrict__ tw, const uint2* __restrict__ itw,
+                                             const uint32_t* __restrict__ qtab,
+                                             const uint32_t* __restrict__ qinv) {
   const int sub = threadIdx.x >> 4, j0 = threadIdx.x & 15;
   const int N = 1 << logN;
-  // ciphertext fastest within a prime: consecutive CTAs reuse the prime's twiddles (and key rows) from L2
-  const int nb = gridDim.y / r;
-  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
   const uint32_t q = __ldg(qtab + p), qi = __ldg(qinv + p);
-  const int c = blockIdx.x * kRowsPerCta + sub;
+  const int c = bx * kRowsPerCta + sub;
   const size_t coff = (size_t)c * kRowLen;
   uint32_t* y0 = Y + ((size_t)b * 2 * r + p) * N + coff;
   uint32_t* y1 = y0 + (size_t)r * N;
@@ -684,6 +708,19 @@ __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __r
     y0[j0 + 16 * k] = x[0][k];
     y1[j0 + 16 * k] = x[1][k];
   }
+}
+
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key(uint32_t* __restrict__ Y,
+                                                                   const uint32_t* __restrict__ K, int krows, int r,
+                                                                   int logN, const uint2* __restrict__ tw,
+                                                                   const uint2* __restrict__ itw,
+                                                                   const uint32_t* __restrict__ qtab,
+                                                                   const uint32_t* __restrict__ qinv) {
+  __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
+  // ciphertext fastest within a prime: consecutive CTAs reuse the prime's twiddles (and key rows) from L2
+  const int nb = gridDim.y / r;
+  const int p = blockIdx.y / nb, b = blockIdx.y - p * nb;
+  rows_key_job(Y, K, krows, r, logN, blockIdx.x, p, b, s, tw, itw, qtab, qinv);
 }
 
 // ------------------------------------------- automorphism in the transform domain
@@ -899,6 +936,190 @@ int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const u
   {
     ProfScope ps(ctx, FHE_K_NTT_INV, 1, st);
     cols_launch(ctx, Y, RowMap{r, r}, nbatch * 2 * r, r, true, st);
+  }
+  return FHE_OK;
+}
+
+// ------------------------------------------------------------ work-table launches
+// One launch runs a transform stage of many ring products of different ring sizes and prime counts
+// (a batch of groups, NttTable).  A CTA takes units u = blockIdx.x, blockIdx.x + gridDim.x, ...; the
+// segment of a unit is found by a forward scan of the segments' first units (u only grows).
+__device__ __forceinline__ int table_seg(const NttTable& t, int u, int si) {
+  while (si + 1 < t.nseg && u >= t.seg[si + 1].unit0) ++si;
+  return si;
+}
+
+// Column stages of rows [y0, y1) of a segment with N1 = 2^LOGN1: (y1 - y0) * 8 column jobs of
+// 2 N1 threads, 256 / N1 of them side by side in the CTA's 512 threads per round (every round is
+// full: 256 / N1 divides 8).  The barrier after a round frees the shared memory for the next.
+template <int LOGN1, bool INV>
+__device__ __forceinline__ void cols_table_rows(const NttSeg& g, int y0, int y1, uint32_t* s) {
+  constexpr int T = 2 << LOGN1, P = 512 / T;
+  const int sub = threadIdx.x / T, tid = threadIdx.x % T;
+  const RowMap rm{g.group_rows, g.group_stride};
+  const int N = 1 << g.logN;
+  uint32_t* ss = s + sub * (T / 2) * 32;
+  for (int j = y0 * 8 + sub; j < y1 * 8; j += P) {
+    if (INV)
+      cols_inv_job<LOGN1>(g.data, rm, g.r, N, j & 7, j >> 3, tid, ss, g.tw, g.q);
+    else
+      cols_fwd_job<LOGN1>(g.data, rm, g.r, N, j & 7, j >> 3, tid, ss, g.tw, g.q);
+    __syncthreads();
+  }
+}
+
+template <int LOGN1, bool INV>
+__device__ __forceinline__ void cols_table_unit(const NttTable& t, int u, int si, uint32_t* s) {
+  const NttSeg& g = t.seg[si];
+  const int y0 = (u - g.unit0) * t.unit_rows;
+  cols_table_rows<LOGN1, INV>(g, y0, min(y0 + t.unit_rows, g.rows), s);
+}
+
+// Persistent: a grid of a few CTAs per SM walks the units (40 registers, 3 CTAs of 512 threads per SM).
+template <bool INV>
+__global__ void __launch_bounds__(512, 3) k_ntt_cols_table(const __grid_constant__ NttTable t) {
+  __shared__ uint32_t s[256 * 32];
+  int si = 0;
+  for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
+    si = table_seg(t, u, si);
+    switch (t.seg[si].logN) {
+      case 13: cols_table_unit<5, INV>(t, u, si, s); break;
+      case 14: cols_table_unit<6, INV>(t, u, si, s); break;
+      case 15: cols_table_unit<7, INV>(t, u, si, s); break;
+      default: cols_table_unit<8, INV>(t, u, si, s); break;
+    }
+  }
+}
+// One round per CTA: unit u of a segment is the 256 / N1 column jobs u (256 / N1) .. of its rows (no
+// loop, 4 CTAs of 512 threads per SM as the one-group kernels).
+template <int LOGN1, bool INV>
+__device__ __forceinline__ void cols_table_round(const NttSeg& g, int v, uint32_t* s) {
+  constexpr int T = 2 << LOGN1, P = 512 / T;
+  const int sub = threadIdx.x / T, j = v * P + sub;
+  const RowMap rm{g.group_rows, g.group_stride};
+  uint32_t* ss = s + sub * (T / 2) * 32;
+  if (INV)
+    cols_inv_job<LOGN1>(g.data, rm, g.r, 1 << g.logN, j & 7, j >> 3, threadIdx.x % T, ss, g.tw, g.q);
+  else
+    cols_fwd_job<LOGN1>(g.data, rm, g.r, 1 << g.logN, j & 7, j >> 3, threadIdx.x % T, ss, g.tw, g.q);
+}
+template <bool INV>
+__global__ void __launch_bounds__(512, 4) k_ntt_cols_table1(const __grid_constant__ NttTable t) {
+  __shared__ uint32_t s[256 * 32];
+  const int si = table_seg(t, blockIdx.x, 0);
+  const NttSeg& g = t.seg[si];
+  const int v = blockIdx.x - g.unit0;
+  switch (g.logN) {
+    case 13: cols_table_round<5, INV>(g, v, s); break;
+    case 14: cols_table_round<6, INV>(g, v, s); break;
+    case 15: cols_table_round<7, INV>(g, v, s); break;
+    default: cols_table_round<8, INV>(g, v, s); break;
+  }
+}
+
+// Fused row passes: unit v of a segment = row block v mod (N / 2048) of by = v / (N / 2048), with
+// prime p = by / nb and ciphertext b = by mod nb (ciphertext fastest within a prime, as in the
+// one-group kernels).  A row's 16 threads own its exchange slots; the warp barrier after a unit
+// orders its last slot reads before the next unit's first writes.
+__global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor_table(const __grid_constant__ NttTable t) {
+  __shared__ uint32_t s[kRowsPerCta * 5 * kSlot];
+  int si = 0;
+  for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
+    si = table_seg(t, u, si);
+    const NttSeg& g = t.seg[si];
+    const int v = u - g.unit0, lb = g.logN - 11;
+    const int by = v >> lb, p = by / g.nb;
+    rows_tensor_job(g.data, g.r, g.logN, v & ((1 << lb) - 1), p, by - p * g.nb, s, g.tw, g.itw, g.q, g.qinv);
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key_table(const __grid_constant__ NttTable t) {
+  __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
+  int si = 0;
+  for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
+    si = table_seg(t, u, si);
+    const NttSeg& g = t.seg[si];
+    const int v = u - g.unit0, lb = g.logN - 11;
+    const int by = v >> lb, p = by / g.nb;
+    rows_key_job(g.data, g.key, g.krows, g.r, g.logN, v & ((1 << lb) - 1), p, by - p * g.nb, s, g.tw, g.itw, g.q,
+                 g.qinv);
+    __syncwarp();
+  }
+}
+
+int launch_ntt_table(const fhe_ctx* prof_ctx, NttTable& t, int stage, int ctas_per_sm, cudaStream_t st) {
+  if (t.nseg < 1 || t.nseg > kTableSegs || stage < kTableColsFwd || stage > kTableRowsKey || ctas_per_sm < 0 ||
+      t.unit_rows < 1) {
+    set_error("ntt_table: bad table (%d segments, stage %d)", t.nseg, stage);
+    return FHE_EINVAL;
+  }
+  const bool cols = stage == kTableColsFwd || stage == kTableColsInv;
+  long long total = 0;
+  for (int i = 0; i < t.nseg; ++i) {
+    NttSeg& g = t.seg[i];
+    if (g.logN < 13 || g.logN > 16 || !g.data || !g.tw || !g.q || g.r < 1 || g.nb < 1 ||
+        (cols && (g.rows < 1 || g.group_rows < 1 || g.group_stride < g.group_rows)) ||
+        (!cols && (!g.itw || !g.qinv)) || (stage == kTableRowsKey && (!g.key || g.krows < g.r))) {
+      set_error("ntt_table: segment %d malformed", i);
+      return FHE_EINVAL;
+    }
+    // columns, one CTA per unit: a unit is one round of 256 / N1 jobs (rows * 8 jobs in all)
+    const long long units = cols ? (ctas_per_sm == 0 ? ((long long)g.rows * 8) >> (16 - g.logN)
+                                                     : (g.rows + t.unit_rows - 1) / t.unit_rows)
+                                 : ((long long)g.nb * g.r) << (g.logN - 11);
+    g.unit0 = (int)total;
+    g.units = (int)units;
+    total += units;
+    if (total > 0x7fffffffLL) {
+      set_error("ntt_table: %lld units exceed one launch", total);
+      return FHE_EINVAL;
+    }
+  }
+  t.total = (int)total;
+  int dev = 0, nsm = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool one = ctas_per_sm == 0;  // columns: the loop-free kernel, one CTA per unit
+  const void* fn = stage == kTableColsFwd   ? (one ? (const void*)k_ntt_cols_table1<false>
+                                                   : (const void*)k_ntt_cols_table<false>)
+                   : stage == kTableColsInv ? (one ? (const void*)k_ntt_cols_table1<true>
+                                                   : (const void*)k_ntt_cols_table<true>)
+                   : stage == kTableRowsTensor ? (const void*)k_ntt_rows_tensor_table
+                                               : (const void*)k_ntt_rows_key_table;
+  const int threads = cols ? 512 : 16 * kRowsPerCta;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, threads, 0);
+  if (e != cudaSuccess) {
+    set_error("ntt_table: %s", cudaGetErrorString(e));
+    return FHE_ECUDA;
+  }
+  long long grid = total;
+  if (ctas_per_sm > 0) {
+    const long long per = ctas_per_sm < fit ? ctas_per_sm : (fit > 0 ? fit : 1);
+    grid = (long long)nsm * per < total ? (long long)nsm * per : total;
+  }
+  const int kclass = stage == kTableColsFwd ? FHE_K_NTT_FWD : stage == kTableColsInv ? FHE_K_NTT_INV : FHE_K_NTT_PW;
+  ProfScope ps(prof_ctx, kclass, 1, st);
+  switch (stage) {
+    case kTableColsFwd:
+      if (one)
+        k_ntt_cols_table1<false><<<(unsigned)grid, 512, 0, st>>>(t);
+      else
+        k_ntt_cols_table<false><<<(unsigned)grid, 512, 0, st>>>(t);
+      break;
+    case kTableColsInv:
+      if (one)
+        k_ntt_cols_table1<true><<<(unsigned)grid, 512, 0, st>>>(t);
+      else
+        k_ntt_cols_table<true><<<(unsigned)grid, 512, 0, st>>>(t);
+      break;
+    case kTableRowsTensor: k_ntt_rows_tensor_table<<<(unsigned)grid, 16 * kRowsPerCta, 0, st>>>(t); break;
+    default: k_ntt_rows_key_table<<<(unsigned)grid, 16 * kRowsPerCta, 0, st>>>(t); break;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("ntt_table: launch failed: %s", cudaGetErrorString(e));
+    return FHE_ECUDA;
   }
   return FHE_OK;
 }

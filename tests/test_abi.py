@@ -70,3 +70,14 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_batch_call_rejects_empty_or_oversized_group_lists_before_touching_the_device():
+    import paper_2607_05920_gb300 as fhe
+
+    assert fhe.lib.fhe_mult_relin_rescale_batch(None, 1, 40, None, None) == fhe.FHE_EINVAL
+    arr = (fhe.FheBatchGroup * 33)()
+    for n in (0, 33):
+        assert fhe.lib.fhe_mult_relin_rescale_batch(arr, n, 40, None, None) == fhe.FHE_EINVAL
+    assert fhe.lib.fhe_mult_relin_rescale_batch(arr, 1, -1, None, None) == fhe.FHE_EINVAL
+    assert b"batch" in fhe.lib.fhe_last_error()

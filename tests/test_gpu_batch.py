@@ -127,3 +127,82 @@ def test_form_search_gives_identical_results_at_the_batched_ring_sizes():
         assert torch.equal(got[i], ref[i].data[0]) and torch.equal(got[i], lev[i]), i
     for p in pairs.values():
         p.ctx.close()
+
+
+def test_work_table_call_equals_per_op_at_every_schedule():
+    """Five ring sizes (2^12 runs per group inside the call, 2^13..2^16 through the work-table launches, all four
+    column-pass shapes), two level buckets on one ring: every schedule of the work-table call, eager and
+    graph-captured, gives the per-op ciphertexts bit for bit; two items match the oracle at their own level."""
+    import torch
+
+    from paper_2607_05920_gb300 import batch
+
+    rings = (12, 13, 14, 15, 16)
+    pairs = {n: make_pair(n, 500, 500, seed=60 + n) for n in rings}
+    ctxs = {n: p.ctx for n, p in pairs.items()}
+    k = 40
+    items = _items(pairs, 8, 57, 100, 500)
+    for n in rings:  # every ring present, one item near the top level
+        items += _items({n: None}, 1, 70 + n, 450, 500)
+    runner = batch.BatchRunner(ctxs, k)
+    sched = {n: [500] for n in rings}
+    sched[14] = [300, 500]
+    plan = runner.plan(items, sched)
+    runner.pack(plan, items)
+    ref = runner.per_op(items)
+    torch.cuda.synchronize()
+    for sc in ((0, 0, 1), (3, 4, 4), (2, 2, 16), (1, 1, 3), None):
+        for g in plan.groups:
+            g.O.zero_()
+        runner.run_table(plan, sc)
+        torch.cuda.synchronize()
+        got = runner.outputs(plan, items)
+        for i, it in enumerate(items):
+            assert torch.equal(got[i], ref[i].data[0]), (sc, i, it.logN, it.logQ)
+    runner.table = (2, 4, 4)
+    runner.capture(plan)
+    for _ in range(2):
+        for g in plan.groups:
+            g.O.zero_()
+        runner.graph.replay()
+        torch.cuda.synchronize()
+        got = runner.outputs(plan, items)
+        assert all(torch.equal(got[i], ref[i].data[0]) for i in range(len(items)))
+    for i in (next(j for j, it in enumerate(items) if it.logN == 13),
+              next(j for j, it in enumerate(items) if it.logN == 15)):
+        it = items[i]
+        P = pairs[it.logN]
+        oa = tuple(bigint.from_limbs(it.a.data.cpu().numpy().view(np.uint32)[0, p]) for p in range(2))
+        ob = tuple(bigint.from_limbs(it.b.data.cpu().numpy().view(np.uint32)[0, p]) for p in range(2))
+        want = ckks.rescale(ckks.mult(oa, ob, P.evk, it.logQ, 500), k, it.logQ)
+        host = got[i].cpu().numpy().view(np.uint32)
+        assert tuple(bigint.from_limbs(host[p]) for p in range(2)) == tuple(want)
+    for p in pairs.values():
+        p.ctx.close()
+
+
+def test_work_table_call_rejects_bad_groups():
+    import torch
+
+    import paper_2607_05920_gb300 as fhe
+    from paper_2607_05920_gb300 import batch
+
+    p = make_pair(13, 300, 300, seed=80)
+    items = _items({13: None}, 2, 81, 100, 300)
+    runner = batch.BatchRunner({13: p.ctx}, 30)
+    plan = runner.plan(items, {13: [150, 300]})
+    if len(plan.groups) < 2:
+        plan = runner.plan(items, {13: [300]})
+    g = plan.groups[0]
+    ws = runner.group_ws(g)
+    base = (p.ctx, g.A, g.B, g.O, g.bits, g.logQ_max)
+    with pytest.raises(fhe.FheError):  # two groups on one workspace
+        fhe.fhe_mult_relin_rescale_batch([base + (ws,), base + (ws,)], 30)
+    with pytest.raises(fhe.FheError):  # out aliases a
+        fhe.fhe_mult_relin_rescale_batch([(p.ctx, g.A, g.B, g.A, g.bits, g.logQ_max, ws)], 30)
+    with pytest.raises(fhe.FheError):  # workspace too small
+        fhe.fhe_mult_relin_rescale_batch([base + (ws[:1024],)], 30)
+    with pytest.raises(fhe.FheError):  # bad schedule
+        fhe.fhe_mult_relin_rescale_batch([base + (ws,)], 30, (1, 1, 0))
+    torch.cuda.synchronize()
+    p.ctx.close()

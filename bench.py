@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--cnum", type=int, default=64, help="ciphertext pairs per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-iters", type=int, default=30)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end to end: timed steps (default: as many as --steps)")
     ap.add_argument("--e2e-sub-batches", type=int, default=E2E_CHUNKS,
                     help="end to end: sub-batches whose upload, compute and download overlap")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrivals per second")
@@ -52,7 +53,10 @@ def parse():
     ap.add_argument("--crt", default="direct", choices=["direct", "garner", "int"],
                     help="RNS->limb reconstruction: exact CRT with rounded quotient (dense sum on the tensor "
                          "cores), Garner mixed radix, or the exact CRT on the integer pipe only")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
+    return args
 
 
 # ----------------------------------------------------------------- oracle side

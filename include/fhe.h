@@ -309,7 +309,7 @@ typedef struct {
  * products, then the same three of the key switches; each group's lifts and
  * reconstructions run per group with its context's kernel forms.  Groups at
  * N <= 2^12 run their transforms per group.  1 <= ngroups <= 32, every
- * context on the current device; sched NULL = {4, 4, 1}.  Profiling of the
+ * context on the current device; sched NULL = {0, 0, 1}.  Profiling of the
  * work-table launches goes to the first group's context. */
 int fhe_mult_relin_rescale_batch(const fhe_batch_group* groups, int ngroups, int k, const fhe_batch_sched* sched,
                                  void* stream);

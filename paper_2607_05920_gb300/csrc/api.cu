@@ -1141,7 +1141,7 @@ int fhe_mult_relin_rescale_batch(const fhe_batch_group* groups, int ngroups, int
     set_error("mult_relin_rescale_batch: bad arguments (%d groups, k %d)", ngroups, k);
     return FHE_EINVAL;
   }
-  const fhe_batch_sched sc = sched ? *sched : fhe_batch_sched{4, 4, 1};
+  const fhe_batch_sched sc = sched ? *sched : fhe_batch_sched{0, 0, 1};
   if (sc.col_ctas_per_sm < 0 || sc.row_ctas_per_sm < 0 || sc.col_unit_rows < 1) {
     set_error("mult_relin_rescale_batch: bad schedule (%d, %d, %d)", sc.col_ctas_per_sm, sc.row_ctas_per_sm,
               sc.col_unit_rows);

@@ -201,8 +201,11 @@ __global__ void k_lift_small(const T* __restrict__ src, size_t src_bstride, uint
 //   T_i = sum_a 256^a S_{i,a},  S_{i,a} = sum_k d_k c_{i,k,a},
 // is congruent to (x - 128 sum_k 256^k) 2^32 mod q_i.  S = A B^T with A the
 // digits of the 128 coefficients of a tile ([128][K = 4L]) and B the
-// constants ([4r][K]); |S| <= 4L 2^14 < 2^22 for L < 64, exact in fp32 and
-// converted to integers by the 1.5 2^23 magic-number addition.  Adding the
+// constants ([4r][K]); |S| <= 4L 2^14 < 2^22 for L < 64, exact in fp32.  One
+// more K column (A: 2048, B: 6144, both exact in f16) adds 1.5 2^23 to every
+// sum inside the GEMM, so the accumulators hold integers in [2^23, 2^24),
+// exact at every partial sum, whose bits are 0x4B400000 + S: the epilogue
+// reads the integers off the bit patterns without a conversion.  Adding the
 // folded offset (and 2^17 q_i) and one Montgomery reduction gives x mod q_i,
 // written as a representative below 2q (the forward transform that follows
 // every lift takes inputs below 4q).
@@ -272,19 +275,30 @@ __global__ void __launch_bounds__(kLtThreads, 1)
   for (int idx = tid; idx < nrows * kcols; idx += kLtThreads) {
     const int p = idx / kcols, kc = idx - p * kcols;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (p < 4 * r)
+    if (p < 4 * r) {
       v = __ldg(reinterpret_cast<const uint4*>(bmat) + (((size_t)(p >> 3) * (4 * kMaxLiftLimbs / 8) + kc) * 8 + (p & 7)));
+      // K = 4L (limb L's digit 0) carries the conversion constant: every B row holds 6144 there, every
+      // A row 2048, so each sum gains 2048 * 6144 = 1.5 2^23 (below)
+      if (kc == L / 2) {
+        if (L & 1)
+          v.z = (v.z & 0xFFFF0000u) | 0x6E00u;
+        else
+          v.x = (v.x & 0xFFFF0000u) | 0x6E00u;
+      }
+    }
     *reinterpret_cast<uint4*>(B + ((size_t)((p >> 3) * kcols + kc) * 8 + (p & 7)) * 16) = v;
   }
   for (int i = tid; i < r; i += kLtThreads) {
     const uint64_t k = __ldg(offL + i);
     PC[i] = make_uint4(__ldg(qtab + i), __ldg(qinv + i), (uint32_t)k, (uint32_t)(k >> 32));
   }
-  // K padding of the digit tile stays zero
+  // K padding of the digit tile stays zero, but for the constant 2048 (f16 0x6800) at K = 4L when L is
+  // even (for odd L the digit producers write it with limb L's digits)
   for (int idx = tid; idx < kLtRows * kcols; idx += kLtThreads) {
     const int t = idx / kcols, kc = idx - t * kcols;
     if (kc >= (L + 1) / 2)
-      *reinterpret_cast<uint4*>(A + (size_t)(t >> 3) * sbo + kc * 128 + (t & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(A + (size_t)(t >> 3) * sbo + kc * 128 + (t & 7) * 16) =
+          make_uint4(kc == L / 2 ? 0x6800u : 0u, 0u, 0u, 0u);
   }
   if (warp == kLtWarpMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
@@ -382,7 +396,10 @@ __global__ void __launch_bounds__(kLtThreads, 1)
             const uint32_t lo = __byte_perm(x, 0x64646464u, 0x5140), hi = __byte_perm(x, 0x64646464u, 0x5342);
             asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u]) : "r"(lo), "r"(0x64806480u));
             asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d[2 * u + 1]) : "r"(hi), "r"(0x64806480u));
-            if (2 * (p0 + jp) + u >= L) d[2 * u] = d[2 * u + 1] = 0u;
+            if (2 * (p0 + jp) + u >= L) {  // no limb: no digits; limb L: the conversion constant
+              d[2 * u] = 2 * (p0 + jp) + u == L ? 0x6800u : 0u;
+              d[2 * u + 1] = 0u;
+            }
           }
           *reinterpret_cast<uint4*>(arow + (p0 + jp) * 128) = make_uint4(d[0], d[1], d[2], d[3]);
         }
@@ -428,11 +445,10 @@ __global__ void __launch_bounds__(kLtThreads, 1)
         for (int j = 0; j < 4; ++j) {
           const int i = i0 + 4 * q4 + j;
           if (i < i1) {
-            // exact integers |S| < 2^22: the bits of S + 1.5 2^23 are 0x4B400000 + S, so
+            // the accumulators hold S + 1.5 2^23 (the constant column), integers in [2^23, 2^24) as
+            // |S| < 2^22, so every partial sum was exact and the bits are 0x4B400000 + S; thus
             // lo = S0 + 256 S1 = a0 + 256 a1 - 257 * 0x4B400000 (mod 2^32, exact as int32)
-            uint32_t sa[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) sa[a] = __float_as_uint(__uint_as_float(v[4 * j + a]) + 12582912.0f);
+            const uint32_t* sa = v + 4 * j;
             const int lo = (int)(sa[0] + (sa[1] << 8) + 0x74C00000u), hi = (int)(sa[2] + (sa[3] << 8) + 0x74C00000u);
             const uint4 k = PC[i];
             const uint64_t u = (uint64_t)((long long)lo + ((long long)hi << 16)) +
@@ -472,7 +488,7 @@ static int lift_tc_launch(const fhe_ctx* ctx, const uint32_t* src, int L, size_t
   LtShape sh;
   sh.r = r;
   sh.L = L;
-  sh.Kpad = 16 * ((4 * L + 15) / 16);
+  sh.Kpad = 16 * ((4 * L + 1 + 15) / 16);  // the digits and the conversion constant's column
   sh.r0 = 4 * ((r + 7) / 8);  // a multiple of 4, so the first half's N is a multiple of 16
   sh.n0 = 4 * sh.r0;
   sh.n1 = r > sh.r0 ? 16 * ((4 * (r - sh.r0) + 15) / 16) : 0;

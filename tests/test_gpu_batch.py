@@ -125,6 +125,14 @@ def test_form_search_gives_identical_results_at_the_batched_ring_sizes():
     torch.cuda.synchronize()
     for i in range(len(items)):
         assert torch.equal(got[i], ref[i].data[0]) and torch.equal(got[i], lev[i]), i
+    # the work-table call at these widths (82 / 123 primes at the top level): the same ciphertexts
+    for sc in ((0, 0, 1), (3, 4, 4)):
+        for g in plan.groups:
+            g.O.zero_()
+        runner.run_table(plan, sc)
+        torch.cuda.synchronize()
+        got = runner.outputs(plan, items)
+        assert all(torch.equal(got[i], ref[i].data[0]) for i in range(len(items))), sc
     for p in pairs.values():
         p.ctx.close()
 

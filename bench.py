@@ -607,7 +607,8 @@ def run_batched(args):
         "group_forms": [[g.logN, g.L_pad, len(g.idx), list(g.forms)] for g in plan.groups],
         "form_timings_ms": form_ms,
         "ring_branches": bool(runner.branches), "branch_timings_ms": branch_ms,
-        "work_table": list(runner.table) if runner.table else None, "table_timings_ms": table_ms,
+        "work_table": list(runner.table) if runner.table else None, "work_table_per_ring": runner.table_per_ring,
+        "table_timings_ms": table_ms,
         "graph_kernels_approx": launches_graph,
         "autotune_ms": {str(k): v for k, v in tuned["timings_ms"].items()},
     }

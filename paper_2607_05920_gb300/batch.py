@@ -98,6 +98,7 @@ class BatchRunner:
         self.graph = None
         self.branches = False  # ring sizes on parallel streams (graph branches); chosen by Autotuner
         self.table = None      # a work-table schedule: all groups in one fhe_mult_relin_rescale_batch call
+        self.table_per_ring = False  # with a schedule: one call per ring size, rings as parallel branches
         self._streams = {}
 
     def plan(self, items: list[Item], schedule: dict) -> Plan:
@@ -153,14 +154,33 @@ class BatchRunner:
             g.ws = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=g.ctx.device)
         return g.ws
 
-    def run_table(self, plan: Plan, sched) -> None:
+    def run_table(self, plan: Plan, sched, per_ring: bool = False) -> None:
         """Every group in one fhe_mult_relin_rescale_batch call: lifts and reconstructions per group (default
-        forms), each transform stage of all groups as one work-table launch with schedule `sched`."""
+        forms), each transform stage of all groups as one work-table launch with schedule `sched`.  With
+        per_ring, one call per ring size, each on that ring's own stream (forked from and joined to the
+        current one, so a captured graph holds the rings as parallel branches)."""
+        torch = self.torch
         for c in {id(g.ctx): g.ctx for g in plan.groups}.values():
             fhe_set_forms(c, *DEFAULT_FORMS)
-        groups = [(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.group_ws(g)) for g in plan.groups]
-        for i in range(0, len(groups), 32):  # at most 32 groups (table segments) per call
-            fhe_mult_relin_rescale_batch(groups[i:i + 32], self.k, sched)
+
+        def call(gs):
+            groups = [(g.ctx, g.A, g.B, g.O, g.bits, g.logQ_max, self.group_ws(g)) for g in gs]
+            for i in range(0, len(groups), 32):  # at most 32 groups (table segments) per call
+                fhe_mult_relin_rescale_batch(groups[i:i + 32], self.k, sched)
+
+        if not per_ring:
+            call(plan.groups)
+            return
+        main = torch.cuda.current_stream()
+        streams = self.branch_streams(plan)
+        used = sorted({g.logN for g in plan.groups})
+        for logN in used:
+            streams[logN].wait_stream(main)
+        for logN in used:
+            with torch.cuda.stream(streams[logN]):
+                call([g for g in plan.groups if g.logN == logN])
+        for logN in used:
+            main.wait_stream(streams[logN])
 
     def run(self, plan: Plan, branches: bool | None = None) -> None:
         """Launch every group (one work-table call when self.table holds a schedule).  With branches, the groups of each ring size go to that ring's own stream
@@ -169,7 +189,7 @@ class BatchRunner:
         so each stream keeps its own workspace."""
         torch = self.torch
         if self.table is not None:
-            self.run_table(plan, self.table)
+            self.run_table(plan, self.table, self.table_per_ring)
             return
         if branches is None:
             branches = self.branches
@@ -341,21 +361,26 @@ class Autotuner:
         torch = runner.torch
         key = self.table_key(torch.cuda.get_device_name(), plan)
         if key in self.cache:
-            runner.table = tuple(self.cache[key]) if self.cache[key] else None
+            v = self.cache[key]
+            runner.table = tuple(v[1:]) if v else None
+            runner.table_per_ring = bool(v[0]) if v else False
             return {}
         timings = {}
-        for sc in TABLE_SCHEDS:
-            runner.run_table(plan, sc)  # warm (and sizes the workspaces)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                runner.run_table(plan, sc)
-            e1.record()
-            e1.synchronize()
-            timings[sc] = e0.elapsed_time(e1) / reps
-        best = min(timings, key=timings.get)
-        report = {"table " + "/".join(map(str, sc)): round(t, 4) for sc, t in timings.items()}
+        for per_ring in (False, True):
+            for sc in TABLE_SCHEDS:
+                runner.run_table(plan, sc, per_ring)  # warm (and sizes the workspaces)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    runner.run_table(plan, sc, per_ring)
+                e1.record()
+                e1.synchronize()
+                timings[(per_ring,) + sc] = e0.elapsed_time(e1) / reps
+        bestk = min(timings, key=timings.get)
+        best, runner.table_per_ring = bestk[1:], bestk[0]
+        report = {("table per ring " if k[0] else "table ") + "/".join(map(str, k[1:])): round(t, 4)
+                  for k, t in timings.items()}
         graphs = {}
         for mode in (best, None):
             runner.table = mode
@@ -372,9 +397,10 @@ class Autotuner:
             del graph
             runner.graph = None
         runner.table = best if graphs[best] < graphs[None] else None
+        runner.table_per_ring = bool(runner.table) and runner.table_per_ring
         report["graph table"] = round(graphs[best], 4)
         report["graph groups"] = round(graphs[None], 4)
-        self.cache[key] = list(runner.table) if runner.table else None
+        self.cache[key] = [int(runner.table_per_ring)] + list(runner.table) if runner.table else None
         self._save()
         return report
 

@@ -159,15 +159,16 @@ def test_work_table_call_equals_per_op_at_every_schedule():
     runner.pack(plan, items)
     ref = runner.per_op(items)
     torch.cuda.synchronize()
-    for sc in ((0, 0, 1), (3, 4, 4), (2, 2, 16), (1, 1, 3), None):
+    for sc, per_ring in (((0, 0, 1), False), ((3, 4, 4), False), ((2, 2, 16), False), ((1, 1, 3), False),
+                         (None, False), ((0, 0, 1), True)):
         for g in plan.groups:
             g.O.zero_()
-        runner.run_table(plan, sc)
+        runner.run_table(plan, sc, per_ring)
         torch.cuda.synchronize()
         got = runner.outputs(plan, items)
         for i, it in enumerate(items):
-            assert torch.equal(got[i], ref[i].data[0]), (sc, i, it.logN, it.logQ)
-    runner.table = (2, 4, 4)
+            assert torch.equal(got[i], ref[i].data[0]), (sc, per_ring, i, it.logN, it.logQ)
+    runner.table, runner.table_per_ring = (2, 4, 4), True  # one call per ring, rings as graph branches
     runner.capture(plan)
     for _ in range(2):
         for g in plan.groups:

@@ -943,8 +943,21 @@ int launch_key_perm(const fhe_ctx* ctx, const uint32_t* AH, uint32_t* Y, const u
 // ------------------------------------------------------------ work-table launches
 // One launch runs a transform stage of many ring products of different ring sizes and prime counts
 // (a batch of groups, NttTable).  A CTA takes units u = blockIdx.x, blockIdx.x + gridDim.x, ...; the
-// segment of a unit is found by a forward scan of the segments' first units (u only grows).
+// segment of its first unit is found by a binary search of the segments' first units, later ones by
+// a forward scan from there (u only grows).
+__device__ __forceinline__ int table_seg_first(const NttTable& t, int u) {
+  int lo = 0, hi = t.nseg - 1;  // the last segment whose first unit is <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.seg[mid].unit0 <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 __device__ __forceinline__ int table_seg(const NttTable& t, int u, int si) {
+  if (si < 0) return table_seg_first(t, u);
   while (si + 1 < t.nseg && u >= t.seg[si + 1].unit0) ++si;
   return si;
 }
@@ -979,7 +992,7 @@ __device__ __forceinline__ void cols_table_unit(const NttTable& t, int u, int si
 template <bool INV>
 __global__ void __launch_bounds__(512, 3) k_ntt_cols_table(const __grid_constant__ NttTable t) {
   __shared__ uint32_t s[256 * 32];
-  int si = 0;
+  int si = -1;
   for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
     si = table_seg(t, u, si);
     switch (t.seg[si].logN) {
@@ -1006,7 +1019,7 @@ __device__ __forceinline__ void cols_table_round(const NttSeg& g, int v, uint32_
 template <bool INV>
 __global__ void __launch_bounds__(512, 4) k_ntt_cols_table1(const __grid_constant__ NttTable t) {
   __shared__ uint32_t s[256 * 32];
-  const int si = table_seg(t, blockIdx.x, 0);
+  const int si = table_seg_first(t, blockIdx.x);
   const NttSeg& g = t.seg[si];
   const int v = blockIdx.x - g.unit0;
   switch (g.logN) {
@@ -1023,7 +1036,7 @@ __global__ void __launch_bounds__(512, 4) k_ntt_cols_table1(const __grid_constan
 // orders its last slot reads before the next unit's first writes.
 __global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor_table(const __grid_constant__ NttTable t) {
   __shared__ uint32_t s[kRowsPerCta * 5 * kSlot];
-  int si = 0;
+  int si = -1;
   for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
     si = table_seg(t, u, si);
     const NttSeg& g = t.seg[si];
@@ -1036,7 +1049,7 @@ __global__ void __launch_bounds__(16 * kRowsPerCta, 4) k_ntt_rows_tensor_table(c
 
 __global__ void __launch_bounds__(16 * kRowsPerCta) k_ntt_rows_key_table(const __grid_constant__ NttTable t) {
   __shared__ uint32_t s[kRowsPerCta * 2 * kSlot];
-  int si = 0;
+  int si = -1;
   for (int u = blockIdx.x; u < t.total; u += gridDim.x) {
     si = table_seg(t, u, si);
     const NttSeg& g = t.seg[si];

@@ -1,9 +1,15 @@
-// RNS -> limb reconstruction with Garner's mixed-radix conversion (Sec. 2
-// Eq. garner_mrc; Sec. 5 "RNS-to-Limb Reconstruction", "Signed Representation
-// Handling") and a fused epilogue (relinearisation rounding, rescale,
-// additions, centring).
+// RNS -> limb reconstruction (Sec. 5 "RNS-to-Limb Reconstruction", "Signed
+// Representation Handling") with a fused epilogue (relinearisation rounding,
+// rescale, additions, centring), in four forms that give identical results:
+//  - k_crt_tc (the default, FHE_CRT_DIRECT / _CVT): the exact direct CRT with
+//    a rounded quotient, its dense sum a byte-digit f16 GEMM on the tcgen05
+//    tensor cores (persistent, warp-specialised; third section below);
+//  - k_crt_direct (FHE_CRT_DIRECT_INT): the same CRT with the dense sum on the
+//    integer pipe (second section);
+//  - k_garner (FHE_CRT_GARNER): Garner's mixed-radix conversion in the nested
+//    order of Sec. 2 Eq. garner_mrc (this section), described below.
 //
-// Per coefficient (one thread each):
+// Garner, per coefficient (one thread each):
 //  1. digits  v_k = | ((x_k - v_0) c_{0,k} - v_1) c_{1,k} - ... ) c_{k-1,k} |_{q_k},
 //     c_{j,k} = [q_j^-1]_{q_k}, in the nested order of Eq. garner_mrc, with
 //     Shoup multiplications by the precomputed constants; digits are kept in

@@ -24,7 +24,10 @@
 // products, inverse NTTs) is three launches: the forward column stages, one
 // fused pass that finishes the forward transforms in each 256-word row, forms
 // the products there and runs the inverse row stages (the transform-domain
-// values never reach global memory), and the inverse column stages.
+// values never reach global memory), and the inverse column stages.  Each
+// of these kernels is a job function plus a one-group launch; the work-table
+// kernels at the end run the same jobs for many groups of ring products (any
+// ring sizes from 2^13 to 2^16 and prime counts) in one launch each.
 #include "common.cuh"
 
 namespace fhe {

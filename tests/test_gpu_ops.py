@@ -97,3 +97,41 @@ def test_mult_plain_decodes_to_the_slot_product():
     dec = bigint.from_limbs(P.ctx.decrypt(out).cpu().numpy().view(np.uint32)[0], signed=True)
     assert np.abs(encode.decode(dec, N, 40, n) - z1 * z2).max() <= 2.0 ** -20
     P.ctx.close()
+
+
+def test_empty_out_of_range_and_degenerate_inputs(p11):
+    """Edge cases through the C ABI: an empty batch (cnum 0) and a level above the context's top are
+    rejected before anything is enqueued, leaving the output untouched; a product of two zero
+    ciphertexts is the zero ciphertext (relinearisation and rescale of zero, rounding included)."""
+    import ctypes
+
+    import torch
+
+    import paper_2607_05920_gb300 as fhe
+
+    ctx = p11.ctx
+    N = 1 << 11
+    a = _ct(fhe, random_ct_limbs(fs.rng(7), 2, N, 120), 120)
+    out = ctx.empty_ct(2, 90)
+    out.data.fill_(-1)
+    before = out.data.clone()
+    ws = ctx.workspace(fhe.FHE_OP_MULT, 120, 2)
+    empty = fhe.FheCt(a.data.data_ptr(), 0, 120, 0, 0.0)
+    eo = fhe.FheCt(out.data.data_ptr(), 0, 90, 0, 0.0)
+    rc = fhe.lib.fhe_mult_relin_rescale(ctx.handle, ctypes.byref(empty), ctypes.byref(empty), 30, ctypes.byref(eo),
+                                        ws.data_ptr(), ws.numel(), None)
+    assert rc == fhe.FHE_EINVAL
+    assert fhe.lib.fhe_rescale(ctx.handle, ctypes.byref(empty), 30, ctypes.byref(eo), None) == fhe.FHE_EINVAL
+    assert fhe.lib.fhe_add(ctx.handle, ctypes.byref(empty), ctypes.byref(empty), ctypes.byref(empty), None) == \
+        fhe.FHE_EINVAL
+    high = fhe.FheCt(a.data.data_ptr(), 2, 121, 0, 0.0)  # above the context's logQ = 120
+    rc = fhe.lib.fhe_mult_relin_rescale(ctx.handle, ctypes.byref(high), ctypes.byref(high), 31, ctypes.byref(
+        fhe.FheCt(out.data.data_ptr(), 2, 90, 0, 0.0)), ws.data_ptr(), ws.numel(), None)
+    assert rc in (fhe.FHE_EINVAL, fhe.FHE_ELEVEL)
+    torch.cuda.synchronize()
+    assert torch.equal(out.data, before)
+    zero = _ct(fhe, np.zeros((2, 2, 4, N), dtype=np.uint32), 120)
+    res = ctx.empty_ct(2, 90)
+    fhe.fhe_mult_relin_rescale(ctx, zero, zero, 30, res)
+    torch.cuda.synchronize()
+    assert int(res.data.abs().sum()) == 0
